@@ -1,0 +1,377 @@
+"""Benchmark of the DiffMPC hot path on GB300: batched forward (SQP) + backward (VJP) solves.
+
+Workload (one "step"): 256 cart-pole OCPs, nx 4, nu 1, T 50, dt 0.05, RK4, 10 SQP
+iterations with the line search, PCG relative-residual tolerance 1e-7, then the VJP of
+l = ||u_0 - u_target||^2 (synthetic seeded inputs, cold start every step).
+
+Prints one JSON line: value = OCP solve+grad per second over all ranks (device time, CUDA
+events), e2e = the same through the autograd API with pinned host inputs, the roofline of
+the dominant kernel, the FP64 CPU oracle's throughput on a sample, clocks, and the
+relative error of the sampled OCPs against the oracle.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "OCP solve+grad/s at ≤1e-4 rel err vs FP64; serving p50/p99 ms vs plain form"
+UNIT = "OCP solve+grad/s"
+B, T, SQP_ITERS, PCG_TOL = 256, 50, 10, 1e-7
+WORKLOAD = "cartpole B=256 nx=4 nu=1 T=50 dt=0.05 RK4, 10 SQP iters + line search, fwd+bwd"
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic FLOPs per knot of the model evaluations (hand count of the cart-pole
+# equations: 25 FLOP per right-hand side, 160 per RK4 step; forward-mode with 5 tangents
+# ~10x; hyper-dual with 2 parameters ~12x).
+F_DYN, F_LIN, F_HD = 160, 1600, 1900
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=256, help="OCPs in the oracle CPU sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(rank):
+    from paper_2510_06179_gb300 import workloads
+    return workloads.cartpole_config(B=B, T=T, seed=1000 + rank, sqp_iters=SQP_ITERS, pcg_tol=PCG_TOL)
+
+
+# ---------------------------------------------------------------------- CPU oracle
+def _single_thread_env():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def _oracle_chunk(args):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    x_s, theta, x_ref, u_t, seed = args
+    from oracle.models import make_model
+    from oracle.ocp import OCPBatch
+    from oracle.sqp import sqp
+    from oracle.backward import vjp
+    ocp = OCPBatch(make_model("cartpole", dt=0.05), T, x_s.astype(np.float64), theta.astype(np.float64),
+                   x_ref.astype(np.float64))
+    out = sqp(ocp, SQP_ITERS, line_search_on=True)
+    z = out["z"]
+    g = np.zeros_like(z)
+    g[:, 4:5] = 2.0 * (z[:, 4:5] - u_t)
+    res = vjp(ocp, z, out["lam"], g)
+    return z, res["dtheta"], out["alpha"]
+
+
+def run_oracle_sample(w, n, pool_size):
+    """Time the FP64 oracle (solve + vjp) on the first n OCPs of the workload, parallel over
+    OCPs on pool_size processes (spawned, one thread each).  Returns (ocp/s, z, dtheta, alpha)."""
+    chunks = []
+    per = max(1, math.ceil(n / pool_size))
+    for s in range(0, n, per):
+        e = min(n, s + per)
+        chunks.append((w.x_s[s:e], w.theta[s:e], w.x_ref[s:e], w.u_target[s:e], s))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(chunks), initializer=_single_thread_env) as pool:
+        pool.map(_oracle_chunk, [(c[0][:1], c[1][:1], c[2][:1], c[3][:1], 0) for c in chunks])  # import warm-up
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_chunk, chunks)
+        dt = time.perf_counter() - t0
+    z = np.concatenate([r[0] for r in res])
+    dth = np.concatenate([r[1] for r in res])
+    al = np.concatenate([r[2] for r in res])
+    return n / dt, z, dth, al, dt
+
+
+# ---------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------- FLOP model
+def algorithmic_flops(pcg_iters_fwd, pcg_iters_bwd, nx=4, nu=1):
+    """Algorithmic FLOPs of one forward launch and one backward launch (per-unit figures in
+    the design notes; PCG counted from measured iteration counts)."""
+    K = T + 1
+    per_iter = K * (12 * nx * nx + 10 * nx)
+    lin = T * F_LIN
+    schur = K * (2 * nx ** 3 + 2 * nx * nx * nu + 4 * nx * nx + 2 * nx * nu)
+    prec = K * (nx ** 3 / 3 + nx ** 3 + 4 * nx ** 3)
+    rec = K * (4 * nx * nx + 2 * nx * nu + 2 * nu * nu)
+    ls = 5 * K * (F_DYN + 2 * (nx + nu))
+    fwd = B * SQP_ITERS * (lin + schur + prec + rec + ls) + per_iter * float(pcg_iters_fwd)
+    bwd = B * (lin + schur + prec + rec + T * F_HD) + per_iter * float(pcg_iters_bwd)
+    return fwd, bwd
+
+
+def alu_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------- main
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    __graft_entry__.build()
+    from paper_2510_06179_gb300.solver import OCPBatch, DiffMPCFunction
+
+    w = workload(rank)
+    # CPU oracle baseline first (spawned pool before the timed GPU region)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n_cpu = min(args.cpu_sample, B)
+        cores = os.cpu_count() or 1
+        rate, z_or, dth_or, al_or, cpu_dt = run_oracle_sample(w, n_cpu, cores)
+        cpu = dict(value=rate, unit=UNIT, cores=cores, kind="oracle",
+                   sample=f"first {n_cpu} of the 256 OCPs (full 10 SQP iterations + VJP each), FP64, "
+                          f"{cores} spawned processes x 1 thread, {cpu_dt:.1f} s")
+    stream = torch.cuda.current_stream(dev)
+    batch = OCPBatch(("cartpole", 4, 1, T, 0.05), batch=B, device=dev, sqp_iters=SQP_ITERS, line_search=1,
+                     pcg_tol=PCG_TOL, warm_start=0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32).reshape(-1)).to(dev)
+    x_s, th, xr, ut = t(w.x_s), t(w.theta), t(w.x_ref), t(w.u_target).view(B, 1)
+    nz = w.n
+    dl = torch.zeros(B * nz, device=dev)
+    out = {"z": torch.empty(B * nz, device=dev), "lam": torch.empty(B * w.m, device=dev),
+           "status": torch.empty(B, dtype=torch.int32, device=dev),
+           "pcg_iters": torch.empty(B * SQP_ITERS, dtype=torch.int32, device=dev),
+           "alpha": torch.empty(B * SQP_ITERS, device=dev)}
+    gout = {"dtheta": torch.empty(w.p * B, device=dev), "dxs": torch.empty(4 * B, device=dev),
+            "lamt": torch.empty(B * w.m, device=dev), "status": torch.empty(B, dtype=torch.int32, device=dev),
+            "pcg_iters": torch.empty(B, dtype=torch.int32, device=dev)}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+
+    def step():
+        batch.solve(x_s, th, xr, out=out)
+        zv = out["z"].view(B, nz)
+        dlv = dl.view(B, nz)
+        dlv[:, 4:5] = 2.0 * (zv[:, 4:5] - ut)
+        batch.vjp(dl, out=gout)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))  # L2 flush between timed iterations (outside the events)
+            ev[i][0].record(stream)
+            batch.solve(x_s, th, xr, out=out)
+            ev[i][1].record(stream)
+            zv = out["z"].view(B, nz)
+            dl.view(B, nz)[:, 4:5] = 2.0 * (zv[:, 4:5] - ut)
+            batch.vjp(dl, out=gout)
+            ev[i][2].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([total_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_s = float(tt.item())
+    value = world * B * args.steps / total_s
+    pcg_f = int(out["pcg_iters"].sum().item())
+    pcg_b = int(gout["pcg_iters"].sum().item())
+    status = out["status"].cpu().numpy()
+
+    # ---- end to end through the public autograd API with pinned host buffers
+    h_xs = torch.from_numpy(w.x_s.reshape(-1).copy()).pin_memory()
+    h_th = torch.from_numpy(w.theta.reshape(-1).copy()).pin_memory()
+    h_xr = torch.from_numpy(w.x_ref.reshape(-1).copy()).pin_memory()
+    h_ut = torch.from_numpy(w.u_target.reshape(-1).copy()).pin_memory()
+    h_gth = torch.empty(w.p * B).pin_memory()
+    h_gxs = torch.empty(4 * B).pin_memory()
+    h_loss = torch.empty(1).pin_memory()
+
+    def e2e_step():
+        d_xs = h_xs.to(dev, non_blocking=True).requires_grad_(True)
+        d_th = h_th.to(dev, non_blocking=True).requires_grad_(True)
+        d_xr = h_xr.to(dev, non_blocking=True)
+        d_ut = h_ut.to(dev, non_blocking=True).view(B, 1)
+        z, _ = DiffMPCFunction.apply(d_xs, d_th, batch, d_xr, None)
+        loss = ((z.view(B, nz)[:, 4:5] - d_ut) ** 2).sum()
+        loss.backward()
+        h_gth.copy_(d_th.grad, non_blocking=True)
+        h_gxs.copy_(d_xs.grad, non_blocking=True)
+        h_loss.copy_(loss.detach().view(1), non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    h2d = (h_xs.numel() + h_th.numel() + h_xr.numel() + h_ut.numel()) * 4
+    d2h = (h_gth.numel() + h_gxs.numel() + 1) * 4
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    clocks = clk.summary()
+    sm_mhz = clocks["sm_mhz"] or 2070.0
+    f_fwd, f_bwd = algorithmic_flops(pcg_f, pcg_b)
+    fwd_avg = float(np.mean(fwd_ms)) / 1e3
+    achieved = f_fwd / fwd_avg / 1e12
+    peak = alu_peak_tflops(sm_mhz)
+    roof = {"bound": "alu", "kernel": "fused_kernel<32,CartPole> (forward, 10 SQP iterations)",
+            "achieved": round(achieved, 4), "peak": round(peak, 2), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 5), "traffic": None,
+            "peak_basis": f"152 SM x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock under load)",
+            "flops_per_launch": f_fwd, "avg_launch_ms": round(fwd_avg * 1e3, 4)}
+    acc = None
+    if cpu is not None:
+        n = z_or.shape[0]
+        zg = out["z"].view(B, nz)[:n].cpu().numpy().astype(np.float64)
+        ag = out["alpha"].view(B, SQP_ITERS)[:n].cpu().numpy()
+        agree = np.all(ag.astype(np.float32) == al_or.astype(np.float32), axis=1)
+        err = np.linalg.norm(zg - z_or, axis=1) / np.linalg.norm(z_or, axis=1)
+        acc = {"checked": int(n), "alpha_path_agree": int(agree.sum()),
+               "z_rel_err_max_agree": float(err[agree].max()) if agree.any() else None,
+               "z_rel_err_median": float(np.median(err)),
+               "within_1e-4": int((err <= 1e-4).sum())}
+    tiling = batch.get_tiling()
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": round(1e3 * total_s / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch_per_gpu": B, "T": T, "sqp_iters": SQP_ITERS,
+                   "pcg_tol": PCG_TOL, "l2": "flushed between timed steps (256 MB write)",
+                   "tiling": tiling, "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "e2e": {"value": round(world * B * args.steps / e2e_s, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * args.steps,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "accuracy": acc,
+        "pcg_iters_per_qp": round(pcg_f / (B * SQP_ITERS), 2),
+        "status_nonzero": int((status & ~4).astype(bool).sum()),
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def reference_arm(args, rank, world):
+    """The FP64 CPU oracle as the reference implementation, timed on the host cores."""
+    if rank != 0:
+        return
+    w = workload(0)
+    cores = os.cpu_count() or 1
+    n = min(args.cpu_sample, B)
+    times = []
+    for _ in range(max(1, args.warmup // 5)):
+        run_oracle_sample(w, min(n, cores), cores)
+    for _ in range(args.steps):
+        rate, *_ , dt = run_oracle_sample(w, n, cores)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps * n / total
+    line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "batch_per_step": n},
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} of the 256 OCPs per step, FP64, {cores} processes x 1 thread"},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * dmpc.h - C-ABI of the GB300 DiffMPC hot path: batched, differentiable solves of
+ *
+ *   OCP:  argmin_{z=(x,u)} sum_{t=0}^{T} c_t^x(x_t) + sum_{t=0}^{T-1} c_t^u(u_t)
+ *         s.t. f_t(x_{t+1}, x_t, u_t) = 0,  x_0 = x_s          (paper Sec. 1 and Sec. 3)
+ *
+ * by SQP (Algorithm 2) whose QPs are solved with the Schur complement S (Eq. 8-10) and
+ * preconditioned conjugate gradient (Algorithm 4), and gradients by the implicit function
+ * theorem (Eq. 3, Eq. 7, Algorithm 3).  All compute runs in CUDA kernels for sm_103a.
+ *
+ * Conventions
+ *  - Pointers passed to dmpc_solve / dmpc_vjp / dmpc_qp_inspect are DEVICE pointers
+ *    (cudaMalloc'd or torch CUDA tensors) owned by the caller, float32, OCPs packed one
+ *    after another at the element offsets returned by dmpc_layout().  The library owns only
+ *    its workspace and the warm-start buffers kept on the device between calls.
+ *  - Per OCP with K = T+1 knots, n = K nx + T nu, m = K nx:
+ *      z      (n)  = (x_0, u_0, x_1, u_1, ..., x_{T-1}, u_{T-1}, x_T)        (Sec. 3.1)
+ *      lambda (m)  = (lambda_0, ..., lambda_T); lambda_0 multiplies x_0 - x_s = 0,
+ *                    lambda_{t+1} multiplies f_t = 0; Lagrangian c + lambda^T g (Eq. 1)
+ *      x_s    (nx), x_ref (K nx) (reference states; NULL means zero)
+ *      theta  (p)  = [model params (p_s) | T x per-knot params (p_k) | diag Q (nx) |
+ *                     diag R (nu) | diag Q_T (nx)],  p = p_s + T p_k + 2 nx + nu
+ *    Costs: c_t^x(x) = 1/2 (x - x_ref,t)^T diag(Q) (x - x_ref,t)  (diag(Q_T) at t = T),
+ *           c_t^u(u) = 1/2 u^T diag(R) u.
+ *  - Models (f_t = x_{t+1} - Phi_t(x_t, u_t), Phi one RK4 / Euler step, or affine):
+ *      LQ           any nx, nu in {(2,1),(3,2),(4,1),(8,4)}; p_s = 0; per knot
+ *                   p_k = nx*nx + nx*nu + nx: Abar_t (row-major), Bbar_t, c_t
+ *      PENDULUM     nx 2, nu 1, params (m, L)                 RK4
+ *      CARTPOLE     nx 4, nu 1, params (m_pole, L), m_cart 1  RK4
+ *      KIN_BICYCLE  nx 4, nu 2, params (wheelbase)            RK4
+ *      SINGLE_TRACK nx 6, nu 2, params (mu, C_alpha)          RK4 (Fiala tyres)
+ *      RIGID_BODY12 nx 12, nu 4, params (m, Jx, Jy, Jz)       RK4
+ *      ATTITUDE     nx 3, nu 3, params (J1, J2, J3)           forward Euler
+ *  - Calls are asynchronous on the handle's CUDA stream and return a dmpc_err for argument
+ *    and launch errors.  Numerical outcomes are per OCP in status_out (bit flags below); a
+ *    failed OCP never aborts the batch and the device never traps.
+ *  - Thread safety: a handle must not be used by two host threads at once.  Calls on one
+ *    handle are ordered by its stream.
+ */
+#ifndef DMPC_H
+#define DMPC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmpc_handle dmpc_handle;
+
+typedef enum {
+  DMPC_OK = 0,
+  DMPC_E_ARG = 1,          /* invalid argument (null pointer, bad size, unknown model) */
+  DMPC_E_OOM = 2,          /* device allocation failed */
+  DMPC_E_BUDGET = 3,       /* request exceeds a memory budget */
+  DMPC_E_CUDA = 4,         /* a CUDA call failed; see dmpc_last_error */
+  DMPC_E_STATE = 5,        /* call out of order (e.g. vjp before any solve) */
+  DMPC_E_UNSUPPORTED = 6   /* model / size combination not compiled in */
+} dmpc_err;
+
+/* per-OCP status bits (status_out) */
+#define DMPC_S_OK 0
+#define DMPC_S_PCG_MAXITER 1     /* a PCG solve hit pcg_max_iters before the tolerance */
+#define DMPC_S_NONFINITE 2       /* a non-finite value appeared in z, lambda or PCG scalars */
+#define DMPC_S_LS_MINSTEP 4      /* no step size passed the decrease test: smallest alpha taken */
+#define DMPC_S_BAD_INPUT 8       /* non-finite cost weight or model parameter */
+#define DMPC_S_PCG_BREAKDOWN 16  /* p^T S p <= 0 in PCG (S not positive definite numerically) */
+#define DMPC_S_CHOL_FAIL 32      /* a diagonal Schur block failed Cholesky (diagonal fallback used) */
+#define DMPC_S_FP64_RESCUE 64    /* informational: a PCG solve whose FP32 iteration stagnated or broke
+                                    down was finished with the operator applied in FP64 */
+
+typedef enum {
+  DMPC_MODEL_LQ = 0,
+  DMPC_MODEL_PENDULUM = 1,
+  DMPC_MODEL_CARTPOLE = 2,
+  DMPC_MODEL_KIN_BICYCLE = 3,
+  DMPC_MODEL_SINGLE_TRACK = 4,
+  DMPC_MODEL_RIGID_BODY12 = 5,
+  DMPC_MODEL_ATTITUDE = 6
+} dmpc_model;
+
+/* One OCP of a batch (the OCP statement of Sec. 3): model, sizes, horizon, step. */
+typedef struct {
+  int model;   /* dmpc_model */
+  int nx, nu;  /* state / input dimension (must match the model) */
+  int T;       /* horizon, 1 <= T <= 4096 */
+  float dt;    /* integrator step (ignored by LQ) */
+} dmpc_ocp_desc;
+
+/* Solver options.  dmpc_default_options() fills the defaults noted here. */
+typedef struct {
+  int sqp_iters;       /* SQP iterations per solve (Algorithm 2); default 1 */
+  int line_search;     /* 1: line search of Algorithm 5; 0: full steps (alpha = 1); default 0 */
+  int n_alpha;         /* number of candidate step sizes, <= 8; default 5 */
+  float alpha[8];      /* candidates in decreasing order; default {1, 0.7, 0.3, 0.1, 0.01} */
+  float ls_eta;        /* decrease-test constant eta of Eq. 14; default 0.4 */
+  float feas_tol;      /* ||g||_1 <= feas_tol (m + ||x||_1) counts as feasible (penalty 0); 1e-5 */
+  float pcg_tol;       /* PCG stops when sqrt(r^T Phi^-1 r / gamma^T Phi^-1 gamma) <= pcg_tol; 1e-9 */
+  int pcg_max_iters;   /* PCG iteration cap per solve; default 1000 */
+  float ru_delta;      /* reliable-update trigger (FP64 true residual when eta drops by delta^2); 0.1 */
+  int warm_start;      /* 1: with z_init == NULL, start from this handle's previous solution and
+                          multipliers, and warm-start the adjoint PCG from the previous one; default 1 */
+  int store_schur;     /* 1: solve keeps the blocks at the returned z for vjp; 0: vjp recomputes; default 0 */
+  int team_threads;    /* threads per OCP: 32, 64, 128 or 256; 0 = chosen from the horizon */
+  int teams_per_block; /* OCPs per thread block; 0 = chosen from batch size and shared memory */
+} dmpc_options;
+
+/* Fill *opt with the defaults above. */
+void dmpc_default_options(dmpc_options* opt);
+
+/* Create a handle for `batch` OCPs (descs[0..batch-1], copied).  opt may be NULL (defaults).
+ * cuda_stream: a cudaStream_t (NULL = default stream).  Allocates the device workspace and
+ * warm-start buffers.  Errors: DMPC_E_ARG, DMPC_E_UNSUPPORTED, DMPC_E_OOM, DMPC_E_CUDA.
+ * On error *out is NULL. */
+dmpc_err dmpc_create_problem_batch(const dmpc_ocp_desc* descs, int batch, const dmpc_options* opt,
+                                   void* cuda_stream, dmpc_handle** out);
+
+/* Element offsets of each OCP in the packed arrays; every pointer may be NULL, each
+ * non-NULL array has batch+1 entries (the last is the total length). */
+dmpc_err dmpc_layout(const dmpc_handle* h, long long* z_off, long long* lam_off, long long* theta_off,
+                     long long* xs_off, long long* xref_off);
+
+/* Forward pass (Algorithm 2): opt.sqp_iters SQP iterations for every OCP of the batch.
+ *   x_s, theta (required), x_ref (NULL = 0): inputs.  The kernel keeps device copies of
+ *     them in the handle for the next dmpc_vjp, so the caller may free them on return.
+ *   z_init (NULL: warm start from the previous solution if opt.warm_start, else the cold
+ *     start x_t = x_s, u_t = 0), lam_init (NULL: previous multipliers or 0).
+ *   z_out (required), lam_out (nullable): solution and multipliers.
+ *   status_out (nullable, batch ints), pcg_iters_out (nullable, batch x sqp_iters ints:
+ *   PCG iterations per QP), alpha_out (nullable, batch x sqp_iters floats: chosen step). */
+dmpc_err dmpc_solve(dmpc_handle* h, const float* x_s, const float* theta, const float* x_ref,
+                    const float* z_init, const float* lam_init, float* z_out, float* lam_out,
+                    int* status_out, int* pcg_iters_out, float* alpha_out);
+
+/* Backward pass (Algorithm 3, Eq. 3 and 7) at the last solution of this handle:
+ *   dl_dz (n per OCP, required) -> dl_dtheta (p per OCP, required), dl_dxs (nx per OCP,
+ *   required), lamt_out (adjoint multipliers, m per OCP, nullable), status_out (nullable),
+ *   pcg_iters_out (nullable, batch ints).  KKT matrix: Gauss-Newton (Sec. 3.4) at the
+ *   returned z.  Error DMPC_E_STATE if no solve preceded it. */
+dmpc_err dmpc_vjp(dmpc_handle* h, const float* dl_dz, float* dl_dtheta, float* dl_dxs, float* lamt_out,
+                  int* status_out, int* pcg_iters_out);
+
+/* Diagnostic: build and solve ONE QP at (z, lam) for every OCP (Eq. 4, 8-11, Algorithm 4)
+ * and write a record per OCP at record + rec_off[b] (rec_off from dmpc_inspect_offsets):
+ *   A_t (T nx nx), B_t (T nx nu), C_t (T nx), g (K nx: x_0 - x_s, f_0..f_{T-1}),
+ *   D, O, Pd, Po (K nx nx each; S_spd and Phi^-1 block rows, O_k couples k to k-1),
+ *   gamma_spd (K nx), lambda+ (K nx), z+ (n), PCG iterations (1).  lam may be NULL (0). */
+dmpc_err dmpc_qp_inspect(dmpc_handle* h, const float* x_s, const float* theta, const float* x_ref,
+                         const float* z, const float* lam, float* record);
+dmpc_err dmpc_inspect_offsets(const dmpc_handle* h, long long* rec_off /* batch+1 */);
+
+/* Change the stream used by later calls. */
+dmpc_err dmpc_set_stream(dmpc_handle* h, void* cuda_stream);
+
+/* Override the tiling: threads per OCP (32/64/128/256) and OCPs per block (>= 1). */
+dmpc_err dmpc_set_tiling(dmpc_handle* h, int team_threads, int teams_per_block);
+
+/* Current tiling and per-team workspace: team threads, teams per block, grid size, dynamic
+ * shared memory bytes per block (0 when the workspace is in global memory). */
+dmpc_err dmpc_get_tiling(const dmpc_handle* h, int* team_threads, int* teams_per_block, int* grid,
+                         long long* smem_bytes);
+
+/* Release the handle and its device memory (synchronises its stream). NULL is ignored. */
+void dmpc_destroy(dmpc_handle* h);
+
+/* Last error message of the handle (or of the last failed create when h is NULL). */
+const char* dmpc_last_error(const dmpc_handle* h);
+
+const char* dmpc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMPC_H */

@@ -1,0 +1,490 @@
+// C-ABI of the DiffMPC CUDA path (declared in include/dmpc.h): handle management, argument
+// validation, layout, tiling choice and kernel launches.  No computation happens on the
+// host; every step of solve / vjp / inspect runs in the fused kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/dmpc.h"
+#include "fused.cuh"
+#include "launch.h"
+
+using namespace dmpc;
+
+namespace {
+
+struct ModelInfo {
+  int nx, nu, p_shared, integ;
+};
+
+bool model_info(int model, int nx, int nu, ModelInfo* mi) {
+  switch (model) {
+    case DMPC_MODEL_LQ:
+      if (!((nx == 2 && nu == 1) || (nx == 3 && nu == 2) || (nx == 4 && nu == 1) || (nx == 8 && nu == 4)))
+        return false;
+      *mi = {nx, nu, 0, I_AFFINE};
+      return true;
+    case DMPC_MODEL_PENDULUM: *mi = {2, 1, 2, I_RK4}; break;
+    case DMPC_MODEL_CARTPOLE: *mi = {4, 1, 2, I_RK4}; break;
+    case DMPC_MODEL_KIN_BICYCLE: *mi = {4, 2, 1, I_RK4}; break;
+    case DMPC_MODEL_SINGLE_TRACK: *mi = {6, 2, 2, I_RK4}; break;
+    case DMPC_MODEL_RIGID_BODY12: *mi = {12, 4, 4, I_RK4}; break;
+    case DMPC_MODEL_ATTITUDE: *mi = {3, 3, 3, I_EULER}; break;
+    default: return false;
+  }
+  return mi->nx == nx && mi->nu == nu;
+}
+
+int p_knot(int model, int nx, int nu) { return model == DMPC_MODEL_LQ ? nx * nx + nx * nu + nx : 0; }
+
+std::mutex g_reg_mu;
+std::vector<KernelEntry> g_registry;
+std::string g_create_error;
+
+const std::vector<KernelEntry>& registry() {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  if (g_registry.empty()) {
+    KernelEntry buf[128];
+    int n = 0;
+    n += register_lq(buf + n);
+    n += register_pendulum(buf + n);
+    n += register_cartpole(buf + n);
+    n += register_bicycle(buf + n);
+    n += register_single_track(buf + n);
+    n += register_rigid_body(buf + n);
+    n += register_attitude(buf + n);
+    n += register_mixed(buf + n);
+    g_registry.assign(buf, buf + n);
+  }
+  return g_registry;
+}
+
+}  // namespace
+
+struct dmpc_handle {
+  int batch = 0;
+  std::vector<dmpc_ocp_desc> descs;
+  dmpc_options opt;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int n_sm = 0;
+  int smem_optin = 0;
+  std::vector<OcpRec> recs;
+  std::vector<int> order;
+  long long tot_z = 0, tot_lam = 0, tot_th = 0, tot_xs = 0, tot_xref = 0, tot_rec = 0, tot_store = 0;
+  std::vector<long long> rec_off;
+  OcpRec* d_recs = nullptr;
+  int* d_order = nullptr;
+  long long* d_rec_off = nullptr;
+  float* res_z = nullptr;
+  double* res_lam = nullptr;
+  float* res_xs = nullptr;
+  float* res_th = nullptr;
+  float* res_xref = nullptr;
+  bool last_had_xref = false;
+  double* res_lamt = nullptr;
+  float* store = nullptr;
+  float* gws = nullptr;
+  size_t gws_floats = 0;
+  bool have_solution = false, have_lamt = false, have_store = false;
+  // tiling
+  bool uniform = true;
+  int model0 = 0, nx0 = 0, nu0 = 0;
+  int max_ws_floats = 0;  // per team, for team_threads
+  int team = 32, tpb = 1, grid = 1;
+  bool use_gws = false;
+  size_t smem = 0;
+  LaunchFn fn = nullptr;
+  std::string err;
+};
+
+static dmpc_err fail(dmpc_handle* h, dmpc_err code, const std::string& msg) {
+  if (h) h->err = msg; else g_create_error = msg;
+  return code;
+}
+
+static dmpc_err cuda_fail(dmpc_handle* h, cudaError_t e, const char* what) {
+  return fail(h, DMPC_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+extern "C" void dmpc_default_options(dmpc_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->sqp_iters = 1;
+  o->line_search = 0;
+  o->n_alpha = 5;
+  const float a[5] = {1.0f, 0.7f, 0.3f, 0.1f, 0.01f};
+  for (int i = 0; i < 5; ++i) o->alpha[i] = a[i];
+  o->ls_eta = 0.4f;
+  o->feas_tol = 1e-5f;
+  o->pcg_tol = 1e-9f;
+  o->pcg_max_iters = 1000;
+  o->ru_delta = 0.1f;
+  o->warm_start = 1;
+  o->store_schur = 0;
+  o->team_threads = 0;
+  o->teams_per_block = 0;
+}
+
+static Options to_kernel_options(const dmpc_options& o) {
+  Options k;
+  std::memset(&k, 0, sizeof(k));
+  k.sqp_iters = o.sqp_iters;
+  k.line_search = o.line_search;
+  k.n_alpha = o.n_alpha;
+  for (int i = 0; i < 8; ++i) k.alpha[i] = o.alpha[i];
+  k.ls_eta = o.ls_eta;
+  k.feas_tol = o.feas_tol;
+  k.pcg_tol = o.pcg_tol;
+  k.pcg_max_iters = o.pcg_max_iters;
+  k.ru_delta = o.ru_delta;
+  return k;
+}
+
+static dmpc_err validate_options(dmpc_handle* h, const dmpc_options& o) {
+  if (o.sqp_iters < 1 || o.sqp_iters > 1000) return fail(h, DMPC_E_ARG, "sqp_iters must be in [1, 1000]");
+  if (o.n_alpha < 1 || o.n_alpha > 8) return fail(h, DMPC_E_ARG, "n_alpha must be in [1, 8]");
+  for (int i = 0; i < o.n_alpha; ++i)
+    if (!(o.alpha[i] > 0.f && o.alpha[i] <= 1.f)) return fail(h, DMPC_E_ARG, "alpha values must be in (0, 1]");
+  if (!(o.ls_eta > 0.f && o.ls_eta < 1.f)) return fail(h, DMPC_E_ARG, "ls_eta must be in (0, 1)");
+  if (!(o.pcg_tol > 0.f && o.pcg_tol < 1.f)) return fail(h, DMPC_E_ARG, "pcg_tol must be in (0, 1)");
+  if (o.pcg_max_iters < 1) return fail(h, DMPC_E_ARG, "pcg_max_iters must be >= 1");
+  if (!(o.ru_delta > 0.f && o.ru_delta < 1.f)) return fail(h, DMPC_E_ARG, "ru_delta must be in (0, 1)");
+  if (!(o.feas_tol >= 0.f)) return fail(h, DMPC_E_ARG, "feas_tol must be >= 0");
+  if (o.team_threads != 0 && o.team_threads != 32 && o.team_threads != 64 && o.team_threads != 128 &&
+      o.team_threads != 256)
+    return fail(h, DMPC_E_ARG, "team_threads must be 0, 32, 64, 128 or 256");
+  if (o.teams_per_block < 0) return fail(h, DMPC_E_ARG, "teams_per_block must be >= 0");
+  return DMPC_OK;
+}
+
+// Pick the kernel and launch shape for (team, tpb); tpb = 0 chooses automatically.
+static dmpc_err configure_tiling(dmpc_handle* h, int team, int tpb) {
+  int maxK = 0;
+  for (auto& d : h->descs) maxK = std::max(maxK, d.T + 1);
+  if (team == 0) team = maxK <= 48 ? 32 : (maxK <= 160 ? 64 : (maxK <= 320 ? 128 : 256));
+  int ws = 0;
+  for (auto& d : h->descs) ws = std::max(ws, make_layout(d.nx, d.nu, d.T + 1, team).total_floats);
+  const size_t ws_bytes = (size_t)ws * sizeof(float);
+  const int max_tpb_threads = 256 / team;
+  h->use_gws = ws_bytes > (size_t)h->smem_optin;
+  int smem_tpb = h->use_gws ? max_tpb_threads : (int)std::max<size_t>(1, (size_t)h->smem_optin / ws_bytes);
+  int cap = std::min(max_tpb_threads, smem_tpb);
+  if (tpb == 0) {
+    tpb = std::max(1, std::min(cap, h->batch / std::max(1, h->n_sm)));
+  }
+  tpb = std::min(tpb, cap);
+  if (tpb < 1) tpb = 1;
+  // find the kernel
+  LaunchFn fn = nullptr;
+  for (auto& e : registry()) {
+    if (e.team != team) continue;
+    if (h->uniform && e.model == h->model0 && e.nx == h->nx0 && e.nu == h->nu0) { fn = e.fn; break; }
+  }
+  if (!fn) {
+    bool has_lq = false;
+    for (auto& d : h->descs) has_lq |= d.model == DMPC_MODEL_LQ;
+    if (has_lq) return fail(h, DMPC_E_UNSUPPORTED, "LQ OCPs cannot be mixed with other models in one batch");
+    for (auto& e : registry())
+      if (e.model == -1 && e.team == team) { fn = e.fn; break; }
+  }
+  if (!fn) return fail(h, DMPC_E_UNSUPPORTED, "no kernel for this model / team size");
+  int grid = (h->batch + tpb - 1) / tpb;
+  if (h->use_gws) {
+    grid = std::min(grid, 2 * h->n_sm);
+    const size_t need = (size_t)grid * tpb * ws;
+    if (need > h->gws_floats) {
+      if (h->gws) cudaFree(h->gws);
+      h->gws = nullptr;
+      cudaError_t e = cudaMalloc(&h->gws, need * sizeof(float));
+      if (e != cudaSuccess) { h->gws_floats = 0; return fail(h, DMPC_E_OOM, "global workspace allocation failed"); }
+      h->gws_floats = need;
+    }
+  }
+  h->team = team;
+  h->tpb = tpb;
+  h->grid = grid;
+  h->max_ws_floats = ws;
+  h->smem = h->use_gws ? 0 : (size_t)tpb * ws_bytes;
+  h->fn = fn;
+  return DMPC_OK;
+}
+
+extern "C" dmpc_err dmpc_create_problem_batch(const dmpc_ocp_desc* descs, int batch, const dmpc_options* opt,
+                                              void* cuda_stream, dmpc_handle** out) {
+  if (!out) return fail(nullptr, DMPC_E_ARG, "out is NULL");
+  *out = nullptr;
+  if (!descs || batch < 1 || batch > (1 << 24)) return fail(nullptr, DMPC_E_ARG, "descs NULL or batch out of range");
+  dmpc_handle* h = new dmpc_handle();
+  if (opt) h->opt = *opt; else dmpc_default_options(&h->opt);
+  dmpc_err er = validate_options(nullptr, h->opt);
+  if (er != DMPC_OK) { delete h; return er; }
+  h->batch = batch;
+  h->descs.assign(descs, descs + batch);
+  h->stream = (cudaStream_t)cuda_stream;
+  cudaError_t ce = cudaGetDevice(&h->device);
+  if (ce != cudaSuccess) { delete h; return cuda_fail(nullptr, ce, "cudaGetDevice"); }
+  cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
+  cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  h->model0 = descs[0].model; h->nx0 = descs[0].nx; h->nu0 = descs[0].nu;
+  h->recs.resize(batch);
+  h->rec_off.resize(batch + 1);
+  std::vector<double> cost(batch);
+  for (int b = 0; b < batch; ++b) {
+    const dmpc_ocp_desc& d = descs[b];
+    ModelInfo mi;
+    if (!model_info(d.model, d.nx, d.nu, &mi)) {
+      delete h;
+      return fail(nullptr, DMPC_E_UNSUPPORTED, "OCP " + std::to_string(b) + ": unknown model or sizes not matching the model");
+    }
+    if (d.T < 1 || d.T > 4096) { delete h; return fail(nullptr, DMPC_E_ARG, "OCP " + std::to_string(b) + ": T must be in [1, 4096]"); }
+    if (d.model != DMPC_MODEL_LQ && !(d.dt > 0.f && std::isfinite(d.dt))) {
+      delete h;
+      return fail(nullptr, DMPC_E_ARG, "OCP " + std::to_string(b) + ": dt must be positive");
+    }
+    h->uniform &= (d.model == h->model0 && d.nx == h->nx0 && d.nu == h->nu0);
+    const int K = d.T + 1;
+    OcpRec& r = h->recs[b];
+    r.model = d.model; r.nx = d.nx; r.nu = d.nu; r.T = d.T; r.dt = d.dt;
+    r.n = K * d.nx + d.T * d.nu;
+    r.m = K * d.nx;
+    r.p = mi.p_shared + d.T * p_knot(d.model, d.nx, d.nu) + 2 * d.nx + d.nu;
+    r.z_off = h->tot_z; h->tot_z += r.n;
+    r.lam_off = h->tot_lam; h->tot_lam += r.m;
+    r.th_off = h->tot_th; h->tot_th += r.p;
+    r.xs_off = h->tot_xs; h->tot_xs += d.nx;
+    r.xref_off = h->tot_xref; h->tot_xref += (long long)K * d.nx;
+    r.gws_off = h->tot_store;
+    h->tot_store += (long long)K * (5 * d.nx * d.nx + d.nx * d.nu);
+    h->rec_off[b] = h->tot_rec;
+    h->tot_rec += (long long)d.T * (d.nx * d.nx + d.nx * d.nu + d.nx) + (long long)K * d.nx +
+                  4LL * K * d.nx * d.nx + 2LL * K * d.nx + r.n + 1;
+    cost[b] = (double)K * d.nx * d.nx * (d.nx + 4);
+  }
+  h->rec_off[batch] = h->tot_rec;
+  h->order.resize(batch);
+  for (int b = 0; b < batch; ++b) h->order[b] = b;
+  std::stable_sort(h->order.begin(), h->order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  // device tables and resident buffers
+  auto dmal = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)); };
+  if (dmal((void**)&h->d_recs, sizeof(OcpRec) * batch) != cudaSuccess ||
+      dmal((void**)&h->d_order, sizeof(int) * batch) != cudaSuccess ||
+      dmal((void**)&h->d_rec_off, sizeof(long long) * (batch + 1)) != cudaSuccess ||
+      dmal((void**)&h->res_z, sizeof(float) * h->tot_z) != cudaSuccess ||
+      dmal((void**)&h->res_lam, sizeof(double) * h->tot_lam) != cudaSuccess ||
+      dmal((void**)&h->res_lamt, sizeof(double) * h->tot_lam) != cudaSuccess ||
+      dmal((void**)&h->res_xs, sizeof(float) * h->tot_xs) != cudaSuccess ||
+      dmal((void**)&h->res_th, sizeof(float) * h->tot_th) != cudaSuccess ||
+      dmal((void**)&h->res_xref, sizeof(float) * h->tot_xref) != cudaSuccess) {
+    dmpc_destroy(h);
+    return fail(nullptr, DMPC_E_OOM, "device allocation failed");
+  }
+  if (h->opt.store_schur) {
+    if (dmal((void**)&h->store, sizeof(float) * h->tot_store) != cudaSuccess) {
+      dmpc_destroy(h);
+      return fail(nullptr, DMPC_E_OOM, "stored-Schur buffer allocation failed");
+    }
+  }
+  ce = cudaMemcpy(h->d_recs, h->recs.data(), sizeof(OcpRec) * batch, cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(h->d_order, h->order.data(), sizeof(int) * batch, cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpy(h->d_rec_off, h->rec_off.data(), sizeof(long long) * (batch + 1), cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) { dmpc_destroy(h); return cuda_fail(nullptr, ce, "table upload"); }
+  er = configure_tiling(h, h->opt.team_threads, h->opt.teams_per_block);
+  if (er != DMPC_OK) {
+    g_create_error = h->err;
+    dmpc_destroy(h);
+    return er;
+  }
+  *out = h;
+  return DMPC_OK;
+}
+
+extern "C" dmpc_err dmpc_layout(const dmpc_handle* h, long long* z_off, long long* lam_off, long long* theta_off,
+                                long long* xs_off, long long* xref_off) {
+  if (!h) return DMPC_E_ARG;
+  for (int b = 0; b <= h->batch; ++b) {
+    const bool last = b == h->batch;
+    if (z_off) z_off[b] = last ? h->tot_z : h->recs[b].z_off;
+    if (lam_off) lam_off[b] = last ? h->tot_lam : h->recs[b].lam_off;
+    if (theta_off) theta_off[b] = last ? h->tot_th : h->recs[b].th_off;
+    if (xs_off) xs_off[b] = last ? h->tot_xs : h->recs[b].xs_off;
+    if (xref_off) xref_off[b] = last ? h->tot_xref : h->recs[b].xref_off;
+  }
+  return DMPC_OK;
+}
+
+extern "C" dmpc_err dmpc_inspect_offsets(const dmpc_handle* h, long long* rec_off) {
+  if (!h || !rec_off) return DMPC_E_ARG;
+  for (int b = 0; b <= h->batch; ++b) rec_off[b] = h->rec_off[b];
+  return DMPC_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static KParams base_params(dmpc_handle* h) {
+  KParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.ocps = h->d_recs;
+  P.order = h->d_order;
+  P.n_work = h->batch;
+  P.opt = to_kernel_options(h->opt);
+  P.ws_floats = h->max_ws_floats;
+  P.gws = h->gws;
+  P.use_gws = h->use_gws ? 1 : 0;
+  P.teams_per_block = h->tpb;
+  return P;
+}
+
+static dmpc_err launch(dmpc_handle* h, const KParams& P) {
+  cudaError_t e = h->fn(P, h->grid, h->team * h->tpb, h->smem, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+  return DMPC_OK;
+}
+
+#define REQUIRE_DEV(ptr, name) \
+  if (!is_device_ptr(ptr)) return fail(h, DMPC_E_ARG, std::string(name) + " must be a device pointer")
+#define OPTIONAL_DEV(ptr, name) \
+  if ((ptr) && !is_device_ptr(ptr)) return fail(h, DMPC_E_ARG, std::string(name) + " must be a device pointer")
+
+extern "C" dmpc_err dmpc_solve(dmpc_handle* h, const float* x_s, const float* theta, const float* x_ref,
+                               const float* z_init, const float* lam_init, float* z_out, float* lam_out,
+                               int* status_out, int* pcg_iters_out, float* alpha_out) {
+  if (!h) return DMPC_E_ARG;
+  REQUIRE_DEV(x_s, "x_s");
+  REQUIRE_DEV(theta, "theta");
+  REQUIRE_DEV(z_out, "z_out");
+  OPTIONAL_DEV(x_ref, "x_ref");
+  OPTIONAL_DEV(z_init, "z_init");
+  OPTIONAL_DEV(lam_init, "lam_init");
+  OPTIONAL_DEV(lam_out, "lam_out");
+  OPTIONAL_DEV(status_out, "status_out");
+  OPTIONAL_DEV(pcg_iters_out, "pcg_iters_out");
+  OPTIONAL_DEV(alpha_out, "alpha_out");
+  KParams P = base_params(h);
+  P.mode = MODE_SOLVE;
+  P.x_s = x_s; P.theta = theta; P.x_ref = x_ref;
+  const bool warm = h->opt.warm_start && h->have_solution;
+  P.z_init = z_init ? z_init : (warm ? h->res_z : nullptr);
+  P.lam_init_f = lam_init;
+  P.lam_init_d = (!lam_init && warm) ? h->res_lam : nullptr;
+  P.z_out = z_out; P.lam_out = lam_out;
+  P.res_z = h->res_z; P.res_lam = h->res_lam;
+  P.res_xs = h->res_xs; P.res_th = h->res_th; P.res_xref = h->res_xref;
+  P.status = status_out; P.pcg_iters = pcg_iters_out; P.alpha_hist = alpha_out;
+  P.store = h->store;
+  P.store_mode = (h->opt.store_schur && h->store) ? 1 : 0;
+  dmpc_err e = launch(h, P);
+  if (e != DMPC_OK) return e;
+  h->have_solution = true;
+  h->have_store = P.store_mode != 0;
+  h->last_had_xref = x_ref != nullptr;
+  return DMPC_OK;
+}
+
+extern "C" dmpc_err dmpc_vjp(dmpc_handle* h, const float* dl_dz, float* dl_dtheta, float* dl_dxs, float* lamt_out,
+                             int* status_out, int* pcg_iters_out) {
+  if (!h) return DMPC_E_ARG;
+  if (!h->have_solution) return fail(h, DMPC_E_STATE, "dmpc_vjp called before any dmpc_solve on this handle");
+  REQUIRE_DEV(dl_dz, "dl_dz");
+  REQUIRE_DEV(dl_dtheta, "dl_dtheta");
+  REQUIRE_DEV(dl_dxs, "dl_dxs");
+  OPTIONAL_DEV(lamt_out, "lamt_out");
+  OPTIONAL_DEV(status_out, "status_out");
+  OPTIONAL_DEV(pcg_iters_out, "pcg_iters_out");
+  KParams P = base_params(h);
+  P.mode = MODE_VJP;
+  // the forward kernel kept copies of its inputs on the device
+  P.x_s = h->res_xs; P.theta = h->res_th; P.x_ref = h->last_had_xref ? h->res_xref : nullptr;
+  P.z_init = h->res_z;
+  P.lam_init_d = h->res_lam;
+  P.dl_dz = dl_dz;
+  P.lamt_init = (h->opt.warm_start && h->have_lamt) ? h->res_lamt : nullptr;
+  P.res_lamt = h->res_lamt;
+  P.dl_dtheta = dl_dtheta; P.dl_dxs = dl_dxs; P.lamt_out = lamt_out;
+  P.status = status_out; P.pcg_iters = pcg_iters_out;
+  P.store = h->store;
+  P.store_mode = h->have_store ? 1 : 0;
+  dmpc_err e = launch(h, P);
+  if (e != DMPC_OK) return e;
+  h->have_lamt = true;
+  return DMPC_OK;
+}
+
+extern "C" dmpc_err dmpc_qp_inspect(dmpc_handle* h, const float* x_s, const float* theta, const float* x_ref,
+                                    const float* z, const float* lam, float* record) {
+  if (!h) return DMPC_E_ARG;
+  REQUIRE_DEV(x_s, "x_s");
+  REQUIRE_DEV(theta, "theta");
+  REQUIRE_DEV(z, "z");
+  REQUIRE_DEV(record, "record");
+  OPTIONAL_DEV(x_ref, "x_ref");
+  OPTIONAL_DEV(lam, "lam");
+  KParams P = base_params(h);
+  P.mode = MODE_INSPECT;
+  P.x_s = x_s; P.theta = theta; P.x_ref = x_ref;
+  P.z_init = z;
+  P.lam_init_f = lam;
+  P.inspect = record;
+  P.inspect_off = h->d_rec_off;
+  return launch(h, P);
+}
+
+extern "C" dmpc_err dmpc_set_stream(dmpc_handle* h, void* s) {
+  if (!h) return DMPC_E_ARG;
+  h->stream = (cudaStream_t)s;
+  return DMPC_OK;
+}
+
+extern "C" dmpc_err dmpc_set_tiling(dmpc_handle* h, int team_threads, int teams_per_block) {
+  if (!h) return DMPC_E_ARG;
+  if (team_threads != 32 && team_threads != 64 && team_threads != 128 && team_threads != 256)
+    return fail(h, DMPC_E_ARG, "team_threads must be 32, 64, 128 or 256");
+  if (teams_per_block < 1 || team_threads * teams_per_block > 256)
+    return fail(h, DMPC_E_ARG, "teams_per_block must be >= 1 with team_threads * teams_per_block <= 256");
+  return configure_tiling(h, team_threads, teams_per_block);
+}
+
+extern "C" dmpc_err dmpc_get_tiling(const dmpc_handle* h, int* team_threads, int* teams_per_block, int* grid,
+                                    long long* smem_bytes) {
+  if (!h) return DMPC_E_ARG;
+  if (team_threads) *team_threads = h->team;
+  if (teams_per_block) *teams_per_block = h->tpb;
+  if (grid) *grid = h->grid;
+  if (smem_bytes) *smem_bytes = (long long)h->smem;
+  return DMPC_OK;
+}
+
+extern "C" void dmpc_destroy(dmpc_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+  cudaFree(h->d_recs);
+  cudaFree(h->d_order);
+  cudaFree(h->d_rec_off);
+  cudaFree(h->res_z);
+  cudaFree(h->res_lam);
+  cudaFree(h->res_lamt);
+  cudaFree(h->res_xs);
+  cudaFree(h->res_th);
+  cudaFree(h->res_xref);
+  cudaFree(h->store);
+  cudaFree(h->gws);
+  delete h;
+}
+
+extern "C" const char* dmpc_last_error(const dmpc_handle* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" const char* dmpc_version(void) { return "dmpc-gb300 0.1 (sm_103a)"; }

@@ -1,0 +1,1247 @@
+// Fused per-OCP SQP iteration and backward pass of DiffMPC (arXiv 2510.06179), one team
+// of threads per OCP, all per-knot data resident in the team's workspace (shared memory,
+// or a global-memory slot when an OCP does not fit).
+//
+// Steps per SQP iteration (Algorithm 2):
+//   a1 linearise every knot in parallel (Eq. 4; Delta-form linear terms)     FP32
+//   a2 Schur blocks chi_t, phi_t (Eq. 10), gamma (App. A.2)                   FP32 / FP64
+//   a3 stair preconditioner Phi^-1 = D^-1 - D^-1 O D^-1 (Eq. 10)              FP32
+//   a4 PCG (Algorithm 4) on S_spd lambda = gamma_spd                          FP32 inner loop,
+//      FP64 solution accumulation with reliable (true-residual) updates
+//   a5 primal recovery (Eq. 11)                                               FP64
+//   a6 line search over the alpha set (Algorithm 5) and the step              FP32 / FP64
+// Backward (Algorithm 3): a1-a3 at the returned z (or stored blocks), adjoint right-hand
+// side from (dl/dz, 0) (Eq. 7), the same PCG, z~ (Eq. 11 form), and
+// dl/dtheta = -(dF/dtheta)^T [z~; lambda~] (Eq. 3) contracted per knot.
+//
+// Data layout in the workspace: element e of knot k of an array lives at arr[e * KP + k]
+// (knot-minor), so the threads of a warp, which own consecutive knots, touch consecutive
+// words.  Thread `lane` of the team owns knots lane, lane + TEAM, ...; knot k holds x_k,
+// u_k, lambda_k, Schur block row k, and the linearisation of dynamics step t = k - 1.
+#pragma once
+#include "device_util.cuh"
+#include "models.cuh"
+#include "params.h"
+
+namespace dmpc {
+
+enum StatusBits : int {
+  ST_OK = 0, ST_PCG_MAXITER = 1, ST_NONFINITE = 2, ST_LS_MINSTEP = 4, ST_BAD_INPUT = 8,
+  ST_PCG_BREAKDOWN = 16, ST_CHOL_FAIL = 32, ST_FP64_RESCUE = 64
+};
+
+constexpr int kMisc = 128;      // per-team scalars (theta, cost weights)
+constexpr int kRedMax = 48;     // must equal Team<>::RED_MAX
+
+struct Layout {
+  int KP;
+  int d_lam, d_lamp, d_gam, d_wx, d_wu, d_r, d_p, d_y, d_total;  // double arrays (in doubles)
+  int x, u, xp, up, f, C, A, Bm, D, O, Pd, Po, r, p, y, dl, misc, red, f_total;  // floats
+  int total_floats;
+};
+
+__host__ __device__ inline Layout make_layout(int nx, int nu, int K, int team) {
+  Layout L;
+  L.KP = (K + 1) & ~1;
+  const int KP = L.KP;
+  int o = 0;
+  L.d_lam = o; o += nx * KP;
+  L.d_lamp = o; o += nx * KP;
+  L.d_gam = o; o += nx * KP;
+  L.d_wx = o; o += nx * KP;
+  L.d_wu = o; o += nu * KP;
+  L.d_r = o; o += nx * KP;
+  L.d_p = o; o += nx * KP;
+  L.d_y = o; o += nx * KP;
+  L.d_total = o;
+  int f = 2 * o;  // floats start after the doubles
+  L.x = f; f += nx * KP;
+  L.u = f; f += nu * KP;
+  L.xp = f; f += nx * KP;
+  L.up = f; f += nu * KP;
+  L.f = f; f += nx * KP;
+  L.C = f; f += nx * KP;
+  L.A = f; f += nx * nx * KP;
+  L.Bm = f; f += nx * nu * KP;
+  L.D = f; f += nx * nx * KP;
+  L.O = f; f += nx * nx * KP;
+  L.Pd = f; f += nx * nx * KP;
+  L.Po = f; f += nx * nx * KP;
+  L.r = f; f += nx * KP;
+  L.p = f; f += nx * KP;
+  L.y = f; f += nx * KP;
+  L.dl = f; f += nx * KP;
+  L.misc = f; f += kMisc;
+  L.red = f; f += 2 * ((team + 31) / 32) * kRedMax;
+  L.f_total = f;
+  L.total_floats = (f + 3) & ~3;
+  return L;
+}
+
+// misc layout (floats): [0,16) shared params, [16,32) raw Q, [32,48) raw R, [48,64) raw Q_T,
+// [64,80) projected Q, [80,96) projected R, [96,112) projected Q_T
+constexpr int MS_TH = 0, MS_Q = 16, MS_R = 32, MS_QT = 48, MS_QP = 64, MS_RP = 80, MS_QTP = 96;
+constexpr int MS_BAD = 120;  // nonzero when a weight or parameter is not finite
+
+template <class M, int TEAM>
+struct Ctx {
+  static constexpr int NX = M::NX, NU = M::NU, NZ = M::NX + M::NU;
+  Team<TEAM> tm;
+  const KParams* P;
+  OcpRec o;
+  Layout L;
+  int K, T, KP, ocp;
+  float dt;
+  double* db;
+  float* fb;
+  int status;
+
+  __device__ __forceinline__ float* F(int off) const { return fb + off; }
+  __device__ __forceinline__ double* Dp(int off) const { return db + off; }
+  __device__ __forceinline__ float misc(int i) const { return fb[L.misc + i]; }
+  __device__ __forceinline__ float qraw(int k, int i) const { return misc((k < T ? MS_Q : MS_QT) + i); }
+  __device__ __forceinline__ float qproj(int k, int i) const { return misc((k < T ? MS_QP : MS_QTP) + i); }
+  __device__ __forceinline__ float xref(int k, int i) const {
+    return P->x_ref ? __ldg(P->x_ref + o.xref_off + (long long)k * NX + i) : 0.f;
+  }
+  // Delta-form linear cost terms (Eq. 4 read in absolute z): q_k = grad c(x_k) - Q_k x_k,
+  // r_k = grad c(u_k) - R u_k, with grad c from the raw weights and Q_k, R projected.
+  __device__ __forceinline__ double qlin(int k, int i, float xk) const {
+    return (double)qraw(k, i) * ((double)xk - (double)xref(k, i)) - (double)qproj(k, i) * (double)xk;
+  }
+  __device__ __forceinline__ double rlin(int i, float uk) const {
+    return (double)misc(MS_R + i) * (double)uk - (double)misc(MS_RP + i) * (double)uk;
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+// small dense helpers on element-major blocks
+template <int NX>
+__device__ __forceinline__ float blk(const float* base, int KP, int k, int i, int j) {
+  return base[(i * NX + j) * KP + k];
+}
+
+// out = Md_k v_k + Mo_k v_{k-1} + Mo_{k+1}^T v_{k+1}  (symmetric block-tridiagonal row k);
+// FP32 blocks, vectors and accumulation in V (float, or double for the FP64 rescue path).
+template <int NX, class V>
+__device__ __forceinline__ void btmv_row(const float* Md, const float* Mo, const V* v, int k, int K,
+                                         int KP, V* out) {
+  V vc[NX], vm[NX], vp[NX];
+#pragma unroll
+  for (int j = 0; j < NX; ++j) {
+    vc[j] = v[j * KP + k];
+    vm[j] = (k > 0) ? v[j * KP + k - 1] : V(0);
+    vp[j] = (k + 1 < K) ? v[j * KP + k + 1] : V(0);
+  }
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    V acc = V(0);
+#pragma unroll
+    for (int j = 0; j < NX; ++j) acc = fma((V)Md[(i * NX + j) * KP + k], vc[j], acc);
+    if (k > 0) {
+#pragma unroll
+      for (int j = 0; j < NX; ++j) acc = fma((V)Mo[(i * NX + j) * KP + k], vm[j], acc);
+    }
+    if (k + 1 < K) {
+#pragma unroll
+      for (int j = 0; j < NX; ++j) acc = fma((V)Mo[(j * NX + i) * KP + k + 1], vp[j], acc);
+    }
+    out[i] = acc;
+  }
+}
+
+// Inverse of an SPD NX x NX block (Cholesky, then L^-T L^-1).  Returns false if a pivot
+// is not positive (the block is then replaced by the inverse of its diagonal).
+template <int NX>
+__device__ bool spd_inverse(const float* a, float* inv) {
+  float L[NX * NX];
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) L[i] = 0.f;
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < NX; ++j) {
+    float s = a[j * NX + j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) s -= L[j * NX + k] * L[j * NX + k];
+    if (!(s > 0.f)) { ok = false; s = fabsf(a[j * NX + j]) + 1e-30f; }
+    float d = sqrtf(s);
+    L[j * NX + j] = d;
+    float id = 1.f / d;
+#pragma unroll
+    for (int i = j + 1; i < NX; ++i) {
+      float t = a[i * NX + j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) t -= L[i * NX + k] * L[j * NX + k];
+      L[i * NX + j] = t * id;
+    }
+  }
+  if (!ok) {
+#pragma unroll
+    for (int i = 0; i < NX * NX; ++i) inv[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) inv[i * NX + i] = 1.f / (fabsf(a[i * NX + i]) + 1e-30f);
+    return false;
+  }
+  // W = L^-1 (lower triangular), forward substitution column by column
+  float W[NX * NX];
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) W[i] = 0.f;
+#pragma unroll
+  for (int c = 0; c < NX; ++c) {
+#pragma unroll
+    for (int i = c; i < NX; ++i) {
+      float t = (i == c) ? 1.f : 0.f;
+#pragma unroll
+      for (int k = c; k < i; ++k) t -= L[i * NX + k] * W[k * NX + c];
+      W[i * NX + c] = t / L[i * NX + i];
+    }
+  }
+  // inv = W^T W
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      float s = 0.f;
+#pragma unroll
+      for (int k = (i > j ? i : j); k < NX; ++k) s += W[k * NX + i] * W[k * NX + j];
+      inv[i * NX + j] = s;
+      inv[j * NX + i] = s;
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// Load per-OCP scalars and the initial iterate.
+template <class M, int TEAM>
+__device__ __noinline__ void stage_load(Ctx<M, TEAM>& c, bool use_z_init) {
+  constexpr int NX = M::NX, NU = M::NU, NZ = NX + NU;
+  const KParams& P = *c.P;
+  const int T = c.T, K = c.K, KP = c.KP;
+  const float* th = P.theta + c.o.th_off;
+  int pk = 0;
+  if constexpr (is_lq<M>::value) pk = M::PK;
+  const int oq = M::NP + T * pk;
+  if (c.tm.lane == 0) {
+    float* ms = c.F(c.L.misc);
+    for (int i = 0; i < M::NP; ++i) ms[MS_TH + i] = th[i];
+    float qm = 0.f, rm = 0.f, qtm = 0.f;
+    for (int i = 0; i < NX; ++i) { ms[MS_Q + i] = th[oq + i]; qm = fmaxf(qm, th[oq + i]); }
+    for (int i = 0; i < NU; ++i) { ms[MS_R + i] = th[oq + NX + i]; rm = fmaxf(rm, th[oq + NX + i]); }
+    for (int i = 0; i < NX; ++i) { ms[MS_QT + i] = th[oq + NX + NU + i]; qtm = fmaxf(qtm, th[oq + NX + NU + i]); }
+    // PD projection of the diagonal Hessians (Sec. 3.1): clamp at 1e-6 max(1, largest entry)
+    float fq = 1e-6f * fmaxf(1.f, qm), fr = 1e-6f * fmaxf(1.f, rm), fqt = 1e-6f * fmaxf(1.f, qtm);
+    int bad = 0;
+    for (int i = 0; i < NX; ++i) { ms[MS_QP + i] = fmaxf(ms[MS_Q + i], fq); bad |= !isfinite(ms[MS_Q + i]); }
+    for (int i = 0; i < NU; ++i) { ms[MS_RP + i] = fmaxf(ms[MS_R + i], fr); bad |= !isfinite(ms[MS_R + i]); }
+    for (int i = 0; i < NX; ++i) { ms[MS_QTP + i] = fmaxf(ms[MS_QT + i], fqt); bad |= !isfinite(ms[MS_QT + i]); }
+    for (int i = 0; i < M::NP; ++i) bad |= !isfinite(ms[MS_TH + i]);
+    ms[MS_BAD] = bad ? 1.f : 0.f;
+  }
+  const float* xs = P.x_s + c.o.xs_off;
+  if (P.mode == MODE_SOLVE && P.res_th) {
+    // keep the inputs of this solve on the device for the backward pass
+    const int p = c.o.p;
+    for (int i = c.tm.lane; i < p; i += TEAM) P.res_th[c.o.th_off + i] = th[i];
+    for (int i = c.tm.lane; i < NX; i += TEAM) P.res_xs[c.o.xs_off + i] = xs[i];
+    if (P.x_ref)
+      for (int i = c.tm.lane; i < K * NX; i += TEAM) P.res_xref[c.o.xref_off + i] = P.x_ref[c.o.xref_off + i];
+  }
+  float* X = c.F(c.L.x);
+  float* U = c.F(c.L.u);
+  double* LAM = c.Dp(c.L.d_lam);
+  const float* zi = use_z_init ? P.z_init : nullptr;
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    const long long zb = c.o.z_off + (long long)k * NZ;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) X[i * KP + k] = zi ? zi[zb + i] : xs[i];
+    if (k < T) {
+#pragma unroll
+      for (int i = 0; i < NU; ++i) U[i * KP + k] = zi ? zi[zb + NX + i] : 0.f;
+    }
+    const long long lb = c.o.lam_off + (long long)k * NX;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      double v = 0.0;
+      if (P.mode != MODE_VJP) {
+        if (P.lam_init_d) v = P.lam_init_d[lb + i];
+        else if (P.lam_init_f) v = (double)P.lam_init_f[lb + i];
+      } else {
+        v = P.lam_init_d ? P.lam_init_d[lb + i] : (P.lam_init_f ? (double)P.lam_init_f[lb + i] : 0.0);
+      }
+      LAM[i * KP + k] = v;
+    }
+  }
+  c.tm.sync();
+  if (c.misc(MS_BAD) != 0.f) c.status |= ST_BAD_INPUT;
+}
+
+// a1: linearise dynamics step t = k-1 at knot slot k (FP32): A_t, B_t, C_t, f_t; f_0 = x_0 - x_s.
+template <class M, int TEAM>
+__device__ __noinline__ void stage_linearise(Ctx<M, TEAM>& c) {
+  constexpr int NX = M::NX, NU = M::NU, NZ = NX + NU;
+  const KParams& P = *c.P;
+  const int T = c.T, K = c.K, KP = c.KP;
+  const float* X = c.F(c.L.x);
+  const float* U = c.F(c.L.u);
+  float* A = c.F(c.L.A);
+  float* Bm = c.F(c.L.Bm);
+  float* C = c.F(c.L.C);
+  float* Fv = c.F(c.L.f);
+  const float* xs = P.x_s + c.o.xs_off;
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    if (k == 0) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) Fv[i * KP] = X[i * KP] - xs[i];
+      continue;
+    }
+    const int t = k - 1;
+    float xt[NX], ut[NU];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) xt[i] = X[i * KP + t];
+#pragma unroll
+    for (int i = 0; i < NU; ++i) ut[i] = U[i * KP + t];
+    float phi[NX];
+    if constexpr (is_lq<M>::value) {
+      const float* tk = P.theta + c.o.th_off + (long long)t * M::PK;
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        float acc = tk[NX * NX + NX * NU + i];
+#pragma unroll
+        for (int j = 0; j < NX; ++j) {
+          float a = tk[i * NX + j];
+          acc = fmaf(a, xt[j], acc);
+          A[(i * NX + j) * KP + k] = -a;
+        }
+#pragma unroll
+        for (int j = 0; j < NU; ++j) {
+          float b = tk[NX * NX + i * NU + j];
+          acc = fmaf(b, ut[j], acc);
+          Bm[(i * NU + j) * KP + k] = -b;
+        }
+        phi[i] = acc;
+        C[i * KP + k] = tk[NX * NX + NX * NU + i];
+      }
+    } else {
+      constexpr int CH = NZ <= 8 ? NZ : 8;
+      float pv[M::NP];
+#pragma unroll
+      for (int j = 0; j < M::NP; ++j) pv[j] = c.misc(MS_TH + j);
+      float cacc[NX];
+#pragma unroll
+      for (int i = 0; i < NX; ++i) cacc[i] = 0.f;
+#pragma unroll
+      for (int c0 = 0; c0 < NZ; c0 += CH) {
+        Dual<CH> xd[NX], ud[NU], pd[M::NP], out[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) xd[i] = Dual<CH>::seed(xt[i], i - c0);
+#pragma unroll
+        for (int i = 0; i < NU; ++i) ud[i] = Dual<CH>::seed(ut[i], NX + i - c0);
+#pragma unroll
+        for (int j = 0; j < M::NP; ++j) pd[j] = Dual<CH>(pv[j]);
+        model_step<M>(xd, ud, pd, c.dt, out);
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+          phi[i] = out[i].v;
+#pragma unroll
+          for (int q = 0; q < CH; ++q) {
+            const int col = c0 + q;
+            if (col < NZ) {
+              const float jv = out[i].d[q];
+              if (col < NX) {
+                A[(i * NX + col) * KP + k] = -jv;
+                cacc[i] = fmaf(jv, xt[col], cacc[i]);
+              } else {
+                Bm[(i * NU + (col - NX)) * KP + k] = -jv;
+                cacc[i] = fmaf(jv, ut[col - NX], cacc[i]);
+              }
+            }
+          }
+        }
+      }
+      // C_t = A^+ x_{t+1} + A_t x_t + B_t u_t - f_t = Phi - J_x x_t - J_u u_t
+#pragma unroll
+      for (int i = 0; i < NX; ++i) C[i * KP + k] = phi[i] - cacc[i];
+    }
+#pragma unroll
+    for (int i = 0; i < NX; ++i) Fv[i * KP + k] = X[i * KP + k] - phi[i];
+  }
+  c.tm.sync();
+}
+
+// a2: Schur blocks of S_spd = H G^-1 H^T (Eq. 10) in FP32:  D_0 = Q_0^-1,
+// D_k = chi_{k-1} = A Q_{k-1}^-1 A^T + B R^-1 B^T + Q_k^-1,  O_k = phi_{k-1} = A Q_{k-1}^-1.
+// With rhs_from_qp, also gamma_spd = -(d + H G^-1 b) (App. A.2) in FP64.
+template <class M, int TEAM>
+__device__ __noinline__ void stage_schur(Ctx<M, TEAM>& c, bool rhs_from_qp) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const KParams& P = *c.P;
+  const int T = c.T, K = c.K, KP = c.KP;
+  const float* A = c.F(c.L.A);
+  const float* Bm = c.F(c.L.Bm);
+  const float* C = c.F(c.L.C);
+  const float* X = c.F(c.L.x);
+  const float* U = c.F(c.L.u);
+  float* D = c.F(c.L.D);
+  float* O = c.F(c.L.O);
+  double* G = c.Dp(c.L.d_gam);
+  const float* xs = P.x_s + c.o.xs_off;
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    float qi[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) qi[i] = 1.f / c.qproj(k, i);
+    if (k == 0) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i)
+#pragma unroll
+        for (int j = 0; j < NX; ++j) D[(i * NX + j) * KP] = (i == j) ? qi[i] : 0.f;
+      if (rhs_from_qp) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i)
+          G[i * KP] = -(double)xs[i] - c.qlin(0, i, X[i * KP]) / (double)c.qproj(0, i);
+      }
+      continue;
+    }
+    const int t = k - 1;
+    float qt[NX], ri[NU];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) qt[i] = 1.f / c.qproj(t, i);
+#pragma unroll
+    for (int i = 0; i < NU; ++i) ri[i] = 1.f / c.misc(MS_RP + i);
+    float a[NX * NX], b[NX * NU];
+#pragma unroll
+    for (int i = 0; i < NX * NX; ++i) a[i] = A[i * KP + k];
+#pragma unroll
+    for (int i = 0; i < NX * NU; ++i) b[i] = Bm[i * KP + k];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+#pragma unroll
+      for (int j = 0; j <= i; ++j) {
+        float s = (i == j) ? qi[i] : 0.f;
+#pragma unroll
+        for (int l = 0; l < NX; ++l) s = fmaf(a[i * NX + l] * qt[l], a[j * NX + l], s);
+#pragma unroll
+        for (int l = 0; l < NU; ++l) s = fmaf(b[i * NU + l] * ri[l], b[j * NU + l], s);
+        D[(i * NX + j) * KP + k] = s;
+        D[(j * NX + i) * KP + k] = s;
+      }
+#pragma unroll
+      for (int j = 0; j < NX; ++j) O[(i * NX + j) * KP + k] = a[i * NX + j] * qt[j];
+    }
+    if (rhs_from_qp) {
+      double vq[NX], vr[NU];
+#pragma unroll
+      for (int j = 0; j < NX; ++j) vq[j] = c.qlin(t, j, X[j * KP + t]) / (double)c.qproj(t, j);
+#pragma unroll
+      for (int j = 0; j < NU; ++j) vr[j] = c.rlin(j, U[j * KP + t]) / (double)c.misc(MS_RP + j);
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        double z = c.qlin(k, i, X[i * KP + k]) / (double)c.qproj(k, i);
+#pragma unroll
+        for (int j = 0; j < NX; ++j) z += (double)a[i * NX + j] * vq[j];
+#pragma unroll
+        for (int j = 0; j < NU; ++j) z += (double)b[i * NU + j] * vr[j];
+        G[i * KP + k] = -(double)C[i * KP + k] - z;
+      }
+    }
+  }
+  c.tm.sync();
+}
+
+// a3: Phi^-1 blocks (FP32): Pd_k = D_k^-1, Po_k = -D_k^-1 O_k D_{k-1}^-1 (Eq. 10).
+template <class M, int TEAM>
+__device__ __noinline__ void stage_precond(Ctx<M, TEAM>& c) {
+  constexpr int NX = M::NX;
+  const int K = c.K, KP = c.KP;
+  const float* D = c.F(c.L.D);
+  const float* O = c.F(c.L.O);
+  float* Pd = c.F(c.L.Pd);
+  float* Po = c.F(c.L.Po);
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    float a[NX * NX], inv[NX * NX];
+#pragma unroll
+    for (int i = 0; i < NX * NX; ++i) a[i] = D[i * KP + k];
+    if (!spd_inverse<NX>(a, inv)) c.status |= ST_CHOL_FAIL;
+#pragma unroll
+    for (int i = 0; i < NX * NX; ++i) Pd[i * KP + k] = inv[i];
+  }
+  c.tm.sync();
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    if (k == 0) continue;
+    float t1[NX * NX];
+    // t1 = O_k Pd_{k-1}
+#pragma unroll
+    for (int i = 0; i < NX; ++i)
+#pragma unroll
+      for (int j = 0; j < NX; ++j) {
+        float s = 0.f;
+#pragma unroll
+        for (int l = 0; l < NX; ++l) s = fmaf(O[(i * NX + l) * KP + k], Pd[(l * NX + j) * KP + k - 1], s);
+        t1[i * NX + j] = s;
+      }
+#pragma unroll
+    for (int i = 0; i < NX; ++i)
+#pragma unroll
+      for (int j = 0; j < NX; ++j) {
+        float s = 0.f;
+#pragma unroll
+        for (int l = 0; l < NX; ++l) s = fmaf(Pd[(i * NX + l) * KP + k], t1[l * NX + j], s);
+        Po[(i * NX + j) * KP + k] = -s;
+      }
+  }
+  c.tm.sync();
+}
+
+// FP64 product S_spd * src evaluated from the factors (H, G^-1) of the current QP data:
+// w = H^T src, then (H G^-1 w).  With res = true it writes the float residual
+// r = float(gamma - S src); otherwise the double product dst = S src.  Leaves w = H^T src in
+// the wx/wu arrays (used by the recovery step).
+template <class M, int TEAM>
+__device__ __noinline__ void hp_apply(Ctx<M, TEAM>& c, const double* src, bool res, double* dst) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const int T = c.T, K = c.K, KP = c.KP;
+  const float* A = c.F(c.L.A);
+  const float* Bm = c.F(c.L.Bm);
+  double* WX = c.Dp(c.L.d_wx);
+  double* WU = c.Dp(c.L.d_wu);
+  const double* G = c.Dp(c.L.d_gam);
+  float* R = c.F(c.L.r);
+  c.tm.sync();
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    double wx[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) wx[i] = src[i * KP + k];
+    if (k < T) {
+      double ln[NX];
+#pragma unroll
+      for (int j = 0; j < NX; ++j) ln[j] = src[j * KP + k + 1];
+      // A_k lives at slot k + 1
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        double s = wx[i];
+#pragma unroll
+        for (int j = 0; j < NX; ++j) s += (double)A[(j * NX + i) * KP + k + 1] * ln[j];
+        wx[i] = s;
+      }
+#pragma unroll
+      for (int i = 0; i < NU; ++i) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < NX; ++j) s += (double)Bm[(j * NU + i) * KP + k + 1] * ln[j];
+        WU[i * KP + k] = s;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NX; ++i) WX[i * KP + k] = wx[i];
+  }
+  c.tm.sync();
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    double s[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) s[i] = WX[i * KP + k] / (double)c.qproj(k, i);
+    if (k > 0) {
+      const int t = k - 1;
+      double vx[NX], vu[NU];
+#pragma unroll
+      for (int j = 0; j < NX; ++j) vx[j] = WX[j * KP + t] / (double)c.qproj(t, j);
+#pragma unroll
+      for (int j = 0; j < NU; ++j) vu[j] = WU[j * KP + t] / (double)c.misc(MS_RP + j);
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        double acc = s[i];
+#pragma unroll
+        for (int j = 0; j < NX; ++j) acc += (double)A[(i * NX + j) * KP + k] * vx[j];
+#pragma unroll
+        for (int j = 0; j < NU; ++j) acc += (double)Bm[(i * NU + j) * KP + k] * vu[j];
+        s[i] = acc;
+      }
+    }
+    if (res) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) R[i * KP + k] = (float)(G[i * KP + k] - s[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) dst[i * KP + k] = s[i];
+    }
+  }
+  c.tm.sync();
+}
+
+template <class M, int TEAM>
+__device__ __forceinline__ void hp_residual(Ctx<M, TEAM>& c, const double* src) {
+  hp_apply<M, TEAM>(c, src, true, nullptr);
+}
+
+// FP64 rescue of a PCG solve (Algorithm 4 with the operator S applied in FP64 from the
+// factors, the preconditioner blocks in FP32, vectors and sums in FP64), continuing from
+// lamp.  Used for the OCPs whose FP32 inner iteration stagnated or broke down.
+template <class M, int TEAM>
+__device__ __noinline__ int stage_pcg64(Ctx<M, TEAM>& c, double eta0, int maxit) {
+  constexpr int NX = M::NX;
+  const KParams& P = *c.P;
+  const int K = c.K, KP = c.KP;
+  const float* Pd = c.F(c.L.Pd);
+  const float* Po = c.F(c.L.Po);
+  double* LP = c.Dp(c.L.d_lamp);
+  double* Rv = c.Dp(c.L.d_r);
+  double* Pv = c.Dp(c.L.d_p);
+  double* Y = c.Dp(c.L.d_y);
+  const double* G = c.Dp(c.L.d_gam);
+  const double tol2 = (double)P.opt.pcg_tol * (double)P.opt.pcg_tol;
+  hp_apply<M, TEAM>(c, LP, false, Y);
+  for (int k = c.tm.lane; k < K; k += TEAM)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) Rv[i * KP + k] = G[i * KP + k] - Y[i * KP + k];
+  c.tm.sync();
+  double e[1] = {0.0};
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    double z[NX];
+    btmv_row<NX, double>(Pd, Po, Rv, k, K, KP, z);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { Pv[i * KP + k] = z[i]; e[0] += Rv[i * KP + k] * z[i]; }
+  }
+  c.tm.sum(e);
+  double eta = e[0];
+  int it = 0;
+  bool converged = !(eta > tol2 * eta0);
+  while (!converged && it < maxit) {
+    hp_apply<M, TEAM>(c, Pv, false, Y);
+    double v[1] = {0.0};
+    for (int k = c.tm.lane; k < K; k += TEAM)
+#pragma unroll
+      for (int i = 0; i < NX; ++i) v[0] += Pv[i * KP + k] * Y[i * KP + k];
+    c.tm.sum(v);
+    if (!(v[0] > 0.0) || !isfinite(v[0])) { c.status |= ST_PCG_BREAKDOWN; break; }
+    const double alpha = eta / v[0];
+    for (int k = c.tm.lane; k < K; k += TEAM)
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        LP[i * KP + k] += alpha * Pv[i * KP + k];
+        Rv[i * KP + k] -= alpha * Y[i * KP + k];
+      }
+    c.tm.sync();
+    double e1[1] = {0.0};
+    for (int k = c.tm.lane; k < K; k += TEAM) {
+      double z[NX];
+      btmv_row<NX, double>(Pd, Po, Rv, k, K, KP, z);
+#pragma unroll
+      for (int i = 0; i < NX; ++i) { Y[i * KP + k] = z[i]; e1[0] += Rv[i * KP + k] * z[i]; }
+    }
+    c.tm.sum(e1);
+    ++it;
+    const double beta = e1[0] / eta;
+    eta = e1[0];
+    if (!(eta > tol2 * eta0)) { converged = true; break; }
+    for (int k = c.tm.lane; k < K; k += TEAM)
+#pragma unroll
+      for (int i = 0; i < NX; ++i) Pv[i * KP + k] = Y[i * KP + k] + beta * Pv[i * KP + k];
+    c.tm.sync();
+  }
+  hp_residual<M, TEAM>(c, LP);  // leaves w = H^T lambda for the recovery
+  if (!converged) c.status |= ST_PCG_MAXITER;
+  return it;
+}
+
+// a4: PCG (Algorithm 4) on S_spd lambda = gamma_spd.  The iteration runs in FP32 on the
+// FP32 blocks; the solution is accumulated in FP64 (lamp) and the residual is replaced by
+// the FP64 true residual whenever eta has dropped by ru_delta^2 since the last
+// replacement, and before convergence is declared (a "reliable update" scheme).
+// Stops when eta <= pcg_tol^2 * eta_0, eta_0 = gamma^T Phi^-1 gamma, on a true residual.
+// On entry lamp holds the initial guess.  Returns the iteration count.
+template <class M, int TEAM>
+__device__ __noinline__ int stage_pcg(Ctx<M, TEAM>& c) {
+  constexpr int NX = M::NX;
+  const KParams& P = *c.P;
+  const int K = c.K, KP = c.KP;
+  const float* D = c.F(c.L.D);
+  const float* O = c.F(c.L.O);
+  const float* Pd = c.F(c.L.Pd);
+  const float* Po = c.F(c.L.Po);
+  float* R = c.F(c.L.r);
+  float* Pv = c.F(c.L.p);
+  float* Y = c.F(c.L.y);
+  float* DL = c.F(c.L.dl);
+  double* LP = c.Dp(c.L.d_lamp);
+  const double* G = c.Dp(c.L.d_gam);
+  const float tol2 = P.opt.pcg_tol * P.opt.pcg_tol;
+  const float dl2 = P.opt.ru_delta * P.opt.ru_delta;
+
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { Y[i * KP + k] = (float)G[i * KP + k]; DL[i * KP + k] = 0.f; }
+  }
+  hp_residual<M, TEAM>(c, LP);
+  float red2[2] = {0.f, 0.f};
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    float rt[NX], gt[NX];
+    btmv_row<NX>(Pd, Po, R, k, K, KP, rt);
+    btmv_row<NX>(Pd, Po, Y, k, K, KP, gt);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      Pv[i * KP + k] = rt[i];
+      red2[0] = fmaf(R[i * KP + k], rt[i], red2[0]);
+      red2[1] = fmaf(Y[i * KP + k], gt[i], red2[1]);
+    }
+  }
+  c.tm.sum(red2);
+  float eta = red2[0];
+  const float eta0 = red2[1];
+  float eta_ref = eta;       // eta at the last true-residual replacement
+  float eta_true = eta;      // last true eta
+  int it = 0, stall = 0;
+  bool converged = !(eta > tol2 * eta0);
+  bool rescue = false;
+  const int maxit = P.opt.pcg_max_iters;
+  bool folded = true;
+  while (!converged && it < maxit) {
+    // y = S p,  v = p^T y
+    float v[1] = {0.f};
+    for (int k = c.tm.lane; k < K; k += TEAM) {
+      float y[NX];
+      btmv_row<NX>(D, O, Pv, k, K, KP, y);
+#pragma unroll
+      for (int i = 0; i < NX; ++i) { Y[i * KP + k] = y[i]; v[0] = fmaf(Pv[i * KP + k], y[i], v[0]); }
+    }
+    c.tm.sum(v);
+    if (!(v[0] > 0.f) || !isfinite(v[0])) { rescue = true; break; }
+    const float alpha = eta / v[0];
+    for (int k = c.tm.lane; k < K; k += TEAM) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        DL[i * KP + k] = fmaf(alpha, Pv[i * KP + k], DL[i * KP + k]);
+        R[i * KP + k] = fmaf(-alpha, Y[i * KP + k], R[i * KP + k]);
+      }
+    }
+    folded = false;
+    c.tm.sync();
+    float e1[1] = {0.f};
+    for (int k = c.tm.lane; k < K; k += TEAM) {
+      float rt[NX];
+      btmv_row<NX>(Pd, Po, R, k, K, KP, rt);
+#pragma unroll
+      for (int i = 0; i < NX; ++i) { Y[i * KP + k] = rt[i]; e1[0] = fmaf(R[i * KP + k], rt[i], e1[0]); }
+    }
+    c.tm.sum(e1);
+    float eta_new = e1[0];
+    ++it;
+    if (eta_new < dl2 * eta_ref || !(eta_new > tol2 * eta0) || it >= maxit || !isfinite(eta_new)) {
+      // reliable update: fold the FP32 correction into the FP64 solution, true residual
+      for (int k = c.tm.lane; k < K; k += TEAM) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) { LP[i * KP + k] += (double)DL[i * KP + k]; DL[i * KP + k] = 0.f; }
+      }
+      folded = true;
+      hp_residual<M, TEAM>(c, LP);
+      float e2[1] = {0.f};
+      for (int k = c.tm.lane; k < K; k += TEAM) {
+        float rt[NX];
+        btmv_row<NX>(Pd, Po, R, k, K, KP, rt);
+#pragma unroll
+        for (int i = 0; i < NX; ++i) { Y[i * KP + k] = rt[i]; e2[0] = fmaf(R[i * KP + k], rt[i], e2[0]); }
+      }
+      c.tm.sum(e2);
+      eta_new = e2[0];
+      eta_ref = eta_new;
+      if (!(eta_new > tol2 * eta0)) { converged = true; break; }
+      if (!isfinite(eta_new)) { rescue = true; break; }
+      // stagnation: a whole update cycle (meant to gain ru_delta^-2) gained less than 4x on the
+      // true residual twice in a row -> the FP32 operator cannot resolve this system
+      if (eta_new > 0.25f * eta_true) {
+        if (++stall >= 2) { rescue = true; break; }
+      } else {
+        stall = 0;
+      }
+      eta_true = eta_new;
+      if (it >= maxit) { rescue = true; break; }
+    }
+    const float beta = eta_new / eta;
+    eta = eta_new;
+    for (int k = c.tm.lane; k < K; k += TEAM) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) Pv[i * KP + k] = fmaf(beta, Pv[i * KP + k], Y[i * KP + k]);
+    }
+    c.tm.sync();
+  }
+  if (!folded) {
+    for (int k = c.tm.lane; k < K; k += TEAM) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) { LP[i * KP + k] += (double)DL[i * KP + k]; DL[i * KP + k] = 0.f; }
+    }
+    hp_residual<M, TEAM>(c, LP);
+  }
+  if (!converged) {
+    // per-OCP FP64 rescue of this solve, continuing from the folded solution
+    c.status |= ST_FP64_RESCUE;
+    it += stage_pcg64<M, TEAM>(c, (double)eta0, maxit);
+  }
+  return it;
+}
+
+// a5: primal recovery (Eq. 11) from lamp and w = H^T lamp (left by the last hp_residual):
+// x_k = -Q_k^-1 (q_k + w_x,k), u_k = -R^-1 (r_k + w_u,k).  Writes float z+ (xp, up).
+template <class M, int TEAM>
+__device__ __noinline__ void stage_recover(Ctx<M, TEAM>& c) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const int T = c.T, K = c.K, KP = c.KP;
+  const float* X = c.F(c.L.x);
+  const float* U = c.F(c.L.u);
+  float* XP = c.F(c.L.xp);
+  float* UP = c.F(c.L.up);
+  const double* WX = c.Dp(c.L.d_wx);
+  const double* WU = c.Dp(c.L.d_wu);
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+#pragma unroll
+    for (int i = 0; i < NX; ++i)
+      XP[i * KP + k] = (float)(-(c.qlin(k, i, X[i * KP + k]) + WX[i * KP + k]) / (double)c.qproj(k, i));
+    if (k < T) {
+#pragma unroll
+      for (int i = 0; i < NU; ++i)
+        UP[i * KP + k] = (float)(-(c.rlin(i, U[i * KP + k]) + WU[i * KP + k]) / (double)c.misc(MS_RP + i));
+    }
+  }
+  c.tm.sync();
+}
+
+template <class M>
+__device__ __forceinline__ void plain_step(const float* tk_lq, const float* pv, float dt, const float* x,
+                                           const float* u, float* xn) {
+  if constexpr (is_lq<M>::value) {
+    constexpr int NX = M::NX, NU = M::NU;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      float acc = tk_lq[NX * NX + NX * NU + i];
+#pragma unroll
+      for (int j = 0; j < NX; ++j) acc = fmaf(tk_lq[i * NX + j], x[j], acc);
+#pragma unroll
+      for (int j = 0; j < NU; ++j) acc = fmaf(tk_lq[NX * NX + i * NU + j], u[j], acc);
+      xn[i] = acc;
+    }
+  } else {
+    model_step<M>(x, u, pv, dt, xn);
+  }
+}
+
+// a6: line search (Algorithm 5; merit Eq. 12, penalty Eq. 13, decrease Eq. 14, descent
+// Eq. 15) over the alpha set, then z <- z + alpha (z+ - z), lambda <- lambda + alpha
+// (lambda+ - lambda).  Cost differences use the exact quadratic expansion, so no large
+// cost values are subtracted.  Returns alpha.
+template <class M, int TEAM>
+__device__ __noinline__ float stage_linesearch(Ctx<M, TEAM>& c) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const KParams& P = *c.P;
+  const int T = c.T, K = c.K, KP = c.KP;
+  float* X = c.F(c.L.x);
+  float* U = c.F(c.L.u);
+  const float* XP = c.F(c.L.xp);
+  const float* UP = c.F(c.L.up);
+  const float* Fv = c.F(c.L.f);
+  double* LAM = c.Dp(c.L.d_lam);
+  const double* LP = c.Dp(c.L.d_lamp);
+  const int na = P.opt.line_search ? P.opt.n_alpha : 0;
+  float alpha = 1.f;
+  if (na > 0) {
+    const float* xs = P.x_s + c.o.xs_off;
+    float pv[M::NP > 0 ? M::NP : 1];
+#pragma unroll
+    for (int j = 0; j < M::NP; ++j) pv[j] = c.misc(MS_TH + j);
+    // red: [num, g0, xabs, dc_0..dc_7, g_0..g_7]
+    double red[19];
+#pragma unroll
+    for (int j = 0; j < 19; ++j) red[j] = 0.0;
+    for (int k = c.tm.lane; k < K; k += TEAM) {
+      double num = 0.0, quad = 0.0;
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        const double xk = X[i * KP + k], dx = (double)XP[i * KP + k] - xk;
+        const double w = c.qraw(k, i);
+        num += w * (xk - (double)c.xref(k, i)) * dx;
+        quad += w * dx * dx;
+        red[1] += fabs((double)Fv[i * KP + k]);
+        red[2] += fabs(xk);
+      }
+      if (k < T) {
+#pragma unroll
+        for (int i = 0; i < NU; ++i) {
+          const double uk = U[i * KP + k], du = (double)UP[i * KP + k] - uk;
+          const double w = c.misc(MS_R + i);
+          num += w * uk * du;
+          quad += w * du * du;
+        }
+      }
+      red[0] += num;
+      const float* tk = nullptr;
+      if constexpr (is_lq<M>::value) {
+        if (k > 0) tk = P.theta + c.o.th_off + (long long)(k - 1) * M::PK;
+      }
+      for (int j = 0; j < na; ++j) {
+        const float a = P.opt.alpha[j];
+        red[3 + j] += (double)a * num + 0.5 * (double)a * (double)a * quad;
+        double g = 0.0;
+        if (k == 0) {
+#pragma unroll
+          for (int i = 0; i < NX; ++i) g += fabs((double)(X[i * KP] + a * (XP[i * KP] - X[i * KP])) - (double)xs[i]);
+        } else {
+          const int t = k - 1;
+          float xa[NX], ua[NU], xn[NX];
+#pragma unroll
+          for (int i = 0; i < NX; ++i) xa[i] = X[i * KP + t] + a * (XP[i * KP + t] - X[i * KP + t]);
+#pragma unroll
+          for (int i = 0; i < NU; ++i) ua[i] = U[i * KP + t] + a * (UP[i * KP + t] - U[i * KP + t]);
+          plain_step<M>(tk, pv, c.dt, xa, ua, xn);
+#pragma unroll
+          for (int i = 0; i < NX; ++i) g += fabs((double)(X[i * KP + k] + a * (XP[i * KP + k] - X[i * KP + k])) - (double)xn[i]);
+        }
+        red[11 + j] += g;
+      }
+    }
+    c.tm.sum(red);
+    const double num = red[0], g0 = red[1], xabs = red[2];
+    const bool feasible = g0 <= (double)P.opt.feas_tol * ((double)(K * NX) + xabs);
+    const double mu = feasible ? 0.0 : fmax(num, 0.0) / (0.5 * g0);
+    const double Dmu = num - mu * g0;
+    float amin = P.opt.alpha[0];
+    for (int j = 0; j < na; ++j) amin = fminf(amin, P.opt.alpha[j]);
+    alpha = amin;
+    bool found = false;
+    for (int j = 0; j < na; ++j) {
+      const double a = P.opt.alpha[j];
+      const double dphi = red[3 + j] + mu * (red[11 + j] - g0) - (double)P.opt.ls_eta * a * Dmu;
+      if (dphi < 0.0) { alpha = P.opt.alpha[j]; found = true; break; }
+    }
+    if (!found) c.status |= ST_LS_MINSTEP;
+    c.tm.sync();
+  }
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      X[i * KP + k] += alpha * (XP[i * KP + k] - X[i * KP + k]);
+      LAM[i * KP + k] += (double)alpha * (LP[i * KP + k] - LAM[i * KP + k]);
+    }
+    if (k < T) {
+#pragma unroll
+      for (int i = 0; i < NU; ++i) U[i * KP + k] += alpha * (UP[i * KP + k] - U[i * KP + k]);
+    }
+  }
+  c.tm.sync();
+  return alpha;
+}
+
+template <class M, int TEAM>
+__device__ void copy_lam_to_lamp(Ctx<M, TEAM>& c) {
+  constexpr int NX = M::NX;
+  const double* LAM = c.Dp(c.L.d_lam);
+  double* LP = c.Dp(c.L.d_lamp);
+  for (int k = c.tm.lane; k < c.K; k += TEAM)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) LP[i * c.KP + k] = LAM[i * c.KP + k];
+  c.tm.sync();
+}
+
+// Write the stored-Schur record of this OCP (A, B, D, O, Pd, Po at the returned z).
+template <class M, int TEAM>
+__device__ __noinline__ void store_blocks(Ctx<M, TEAM>& c, bool load) {
+  constexpr int NX = M::NX, NU = M::NU;
+  float* dst = c.P->store + c.o.gws_off;
+  const int K = c.K, KP = c.KP;
+  const int offs[6] = {c.L.A, c.L.Bm, c.L.D, c.L.O, c.L.Pd, c.L.Po};
+  const int sizes[6] = {NX * NX, NX * NU, NX * NX, NX * NX, NX * NX, NX * NX};
+  long long base = 0;
+  for (int a = 0; a < 6; ++a) {
+    float* w = c.F(offs[a]);
+    for (int e = 0; e < sizes[a]; ++e) {
+      for (int k = c.tm.lane; k < K; k += TEAM) {
+        if (load) w[e * KP + k] = dst[base + (long long)e * K + k];
+        else dst[base + (long long)e * K + k] = w[e * KP + k];
+      }
+    }
+    base += (long long)sizes[a] * K;
+  }
+  c.tm.sync();
+}
+
+template <class M, int TEAM>
+__device__ __noinline__ void write_inspect(Ctx<M, TEAM>& c, int iters) {
+  constexpr int NX = M::NX, NU = M::NU, NZ = NX + NU;
+  const int T = c.T, K = c.K, KP = c.KP;
+  float* out = c.P->inspect + c.P->inspect_off[c.ocp];
+  // record: A (T nx nx), B (T nx nu), C (T nx), f (K nx), D, O, Pd, Po (K nx nx each),
+  // gamma (K nx), lambda+ (K nx), z+ (n), pcg iterations (1); knot-major, row-major blocks
+  long long o = 0;
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    if (k >= 1) {
+      const int t = k - 1;
+      for (int e = 0; e < NX * NX; ++e) out[o + (long long)t * NX * NX + e] = c.F(c.L.A)[e * KP + k];
+      for (int e = 0; e < NX * NU; ++e) out[o + (long long)T * NX * NX + (long long)t * NX * NU + e] = c.F(c.L.Bm)[e * KP + k];
+      for (int e = 0; e < NX; ++e) out[o + (long long)T * (NX * NX + NX * NU) + (long long)t * NX + e] = c.F(c.L.C)[e * KP + k];
+    }
+  }
+  o += (long long)T * (NX * NX + NX * NU + NX);
+  const int blks[4] = {c.L.D, c.L.O, c.L.Pd, c.L.Po};
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    for (int e = 0; e < NX; ++e) out[o + (long long)k * NX + e] = c.F(c.L.f)[e * KP + k];
+    for (int b = 0; b < 4; ++b)
+      for (int e = 0; e < NX * NX; ++e)
+        out[o + (long long)K * NX + (long long)b * K * NX * NX + (long long)k * NX * NX + e] = c.F(blks[b])[e * KP + k];
+    const long long og = o + (long long)K * NX + 4LL * K * NX * NX;
+    for (int e = 0; e < NX; ++e) {
+      out[og + (long long)k * NX + e] = (float)c.Dp(c.L.d_gam)[e * KP + k];
+      out[og + (long long)K * NX + (long long)k * NX + e] = (float)c.Dp(c.L.d_lamp)[e * KP + k];
+    }
+    const long long oz = og + 2LL * K * NX;
+    for (int e = 0; e < NX; ++e) out[oz + (long long)k * NZ + e] = c.F(c.L.xp)[e * KP + k];
+    if (k < T)
+      for (int e = 0; e < NU; ++e) out[oz + (long long)k * NZ + NX + e] = c.F(c.L.up)[e * KP + k];
+    if (k == 0) out[oz + (long long)K * NX + (long long)T * NU] = (float)iters;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Forward: the SQP iterations of one OCP (or one QP in inspect mode).
+template <class M, int TEAM>
+__device__ void run_forward(Ctx<M, TEAM>& c) {
+  constexpr int NX = M::NX, NU = M::NU, NZ = NX + NU;
+  const KParams& P = *c.P;
+  const int T = c.T, K = c.K, KP = c.KP;
+  stage_load<M, TEAM>(c, P.z_init != nullptr);
+  const int iters = (P.mode == MODE_INSPECT) ? 1 : P.opt.sqp_iters;
+  for (int s = 0; s < iters; ++s) {
+    stage_linearise<M, TEAM>(c);
+    stage_schur<M, TEAM>(c, true);
+    stage_precond<M, TEAM>(c);
+    copy_lam_to_lamp<M, TEAM>(c);
+    const int it = stage_pcg<M, TEAM>(c);
+    stage_recover<M, TEAM>(c);
+    if (P.mode == MODE_INSPECT) { write_inspect<M, TEAM>(c, it); break; }
+    const float a = stage_linesearch<M, TEAM>(c);
+    if (c.tm.lane == 0) {
+      if (P.pcg_iters) P.pcg_iters[(long long)c.ocp * P.opt.sqp_iters + s] = it;
+      if (P.alpha_hist) P.alpha_hist[(long long)c.ocp * P.opt.sqp_iters + s] = a;
+    }
+  }
+  if (P.mode == MODE_INSPECT) return;
+  if (P.store_mode && P.store) {
+    // stored-Schur mode: re-linearise at the returned z and keep the blocks for the vjp
+    stage_linearise<M, TEAM>(c);
+    stage_schur<M, TEAM>(c, false);
+    stage_precond<M, TEAM>(c);
+    store_blocks<M, TEAM>(c, false);
+  }
+  const float* X = c.F(c.L.x);
+  const float* U = c.F(c.L.u);
+  const double* LAM = c.Dp(c.L.d_lam);
+  int bad = 0;
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    const long long zb = c.o.z_off + (long long)k * NZ;
+    const long long lb = c.o.lam_off + (long long)k * NX;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      const float xv = X[i * KP + k];
+      bad |= !isfinite(xv);
+      P.z_out[zb + i] = xv;
+      if (P.res_z) P.res_z[zb + i] = xv;
+      const double lv = LAM[i * KP + k];
+      bad |= !isfinite(lv);
+      if (P.lam_out) P.lam_out[lb + i] = (float)lv;
+      if (P.res_lam) P.res_lam[lb + i] = lv;
+    }
+    if (k < T) {
+#pragma unroll
+      for (int i = 0; i < NU; ++i) {
+        const float uv = U[i * KP + k];
+        bad |= !isfinite(uv);
+        P.z_out[zb + NX + i] = uv;
+        if (P.res_z) P.res_z[zb + NX + i] = uv;
+      }
+    }
+  }
+  float fb[1] = {(float)bad};
+  c.tm.sum(fb);
+  if (fb[0] > 0.f) c.status |= ST_NONFINITE;
+  if (c.tm.lane == 0 && P.status) P.status[c.ocp] = c.status;
+}
+
+// Backward (Algorithm 3): adjoint PCG with the same S, z~, and the theta contraction.
+template <class M, int TEAM>
+__device__ __noinline__ void run_backward(Ctx<M, TEAM>& c) {
+  constexpr int NX = M::NX, NU = M::NU, NZ = NX + NU, NP = M::NP;
+  const KParams& P = *c.P;
+  const int T = c.T, K = c.K, KP = c.KP;
+  stage_load<M, TEAM>(c, true);   // z (returned solution) and lambda (forward multipliers)
+  if (P.store_mode && P.store) {
+    store_blocks<M, TEAM>(c, true);
+  } else {
+    stage_linearise<M, TEAM>(c);
+    stage_schur<M, TEAM>(c, false);
+    stage_precond<M, TEAM>(c);
+  }
+  // adjoint right-hand side: gamma~_spd = H G^-1 dl/dz (Eq. 7 with (-b, d) <- (dl/dz, 0))
+  const float* g = P.dl_dz + c.o.z_off;
+  const float* A = c.F(c.L.A);
+  const float* Bm = c.F(c.L.Bm);
+  double* G = c.Dp(c.L.d_gam);
+  double* LP = c.Dp(c.L.d_lamp);
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    double s[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) s[i] = (double)g[(long long)k * NZ + i] / (double)c.qproj(k, i);
+    if (k > 0) {
+      const int t = k - 1;
+      double vx[NX], vu[NU];
+#pragma unroll
+      for (int j = 0; j < NX; ++j) vx[j] = (double)g[(long long)t * NZ + j] / (double)c.qproj(t, j);
+#pragma unroll
+      for (int j = 0; j < NU; ++j) vu[j] = (double)g[(long long)t * NZ + NX + j] / (double)c.misc(MS_RP + j);
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+#pragma unroll
+        for (int j = 0; j < NX; ++j) s[i] += (double)A[(i * NX + j) * KP + k] * vx[j];
+#pragma unroll
+        for (int j = 0; j < NU; ++j) s[i] += (double)Bm[(i * NU + j) * KP + k] * vu[j];
+      }
+    }
+    const long long lb = c.o.lam_off + (long long)k * NX;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      G[i * KP + k] = s[i];
+      LP[i * KP + k] = P.lamt_init ? P.lamt_init[lb + i] : 0.0;
+    }
+  }
+  c.tm.sync();
+  const int it = stage_pcg<M, TEAM>(c);
+  // z~ = G^-1 (dl/dz - H^T lambda~)  (stored in xp, up)
+  const double* WX = c.Dp(c.L.d_wx);
+  const double* WU = c.Dp(c.L.d_wu);
+  float* XT = c.F(c.L.xp);
+  float* UT = c.F(c.L.up);
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+#pragma unroll
+    for (int i = 0; i < NX; ++i)
+      XT[i * KP + k] = (float)(((double)g[(long long)k * NZ + i] - WX[i * KP + k]) / (double)c.qproj(k, i));
+    if (k < T) {
+#pragma unroll
+      for (int i = 0; i < NU; ++i)
+        UT[i * KP + k] = (float)(((double)g[(long long)k * NZ + NX + i] - WU[i * KP + k]) / (double)c.misc(MS_RP + i));
+    }
+  }
+  c.tm.sync();
+  // theta contraction: dl/dtheta = -(dF/dtheta)^T [z~; lambda~]
+  const float* X = c.F(c.L.x);
+  const float* U = c.F(c.L.u);
+  const double* LAM = c.Dp(c.L.d_lam);
+  constexpr int NR = NP + NX + NU + NX;
+  float red[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) red[j] = 0.f;
+  float* dth = P.dl_dtheta + c.o.th_off;
+  int pk = 0;
+  if constexpr (is_lq<M>::value) pk = M::PK;
+  const int oq = NP + T * pk;
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    // cost part: grad c^x = Q (x - xref), grad c^u = R u
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      const float v = XT[i * KP + k] * (X[i * KP + k] - c.xref(k, i));
+      if (k < T) red[NP + i] -= v; else red[NP + NX + NU + i] -= v;
+    }
+    if (k < T) {
+#pragma unroll
+      for (int i = 0; i < NU; ++i) red[NP + NX + i] -= UT[i * KP + k] * U[i * KP + k];
+    }
+    if (k == 0) continue;
+    const int t = k - 1;
+    if constexpr (is_lq<M>::value) {
+      float* dk = dth + (long long)t * M::PK;
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        const float li = (float)LAM[i * KP + k], lti = (float)LP[i * KP + k];
+#pragma unroll
+        for (int j = 0; j < NX; ++j) dk[i * NX + j] = li * XT[j * KP + t] + lti * X[j * KP + t];
+#pragma unroll
+        for (int j = 0; j < NU; ++j) dk[NX * NX + i * NU + j] = li * UT[j * KP + t] + lti * U[j * KP + t];
+        dk[NX * NX + NX * NU + i] = lti;
+      }
+    } else {
+      HDual<NP> xh[NX], uh[NU], ph[NP], out[NX];
+#pragma unroll
+      for (int i = 0; i < NX; ++i) { xh[i] = HDual<NP>(X[i * KP + t]); xh[i].e = XT[i * KP + t]; }
+#pragma unroll
+      for (int i = 0; i < NU; ++i) { uh[i] = HDual<NP>(U[i * KP + t]); uh[i].e = UT[i * KP + t]; }
+#pragma unroll
+      for (int j = 0; j < NP; ++j) { ph[j] = HDual<NP>(c.misc(MS_TH + j)); ph[j].t[j] = 1.f; }
+      model_step<M>(xh, uh, ph, c.dt, out);
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        const float li = (float)LAM[i * KP + k], lti = (float)LP[i * KP + k];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) red[j] = fmaf(li, out[i].et[j], fmaf(lti, out[i].t[j], red[j]));
+      }
+    }
+  }
+  c.tm.sum(red);
+  if (c.tm.lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NP; ++j) dth[j] = red[j];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { dth[oq + i] = red[NP + i]; dth[oq + NX + NU + i] = red[NP + NX + NU + i]; }
+#pragma unroll
+    for (int i = 0; i < NU; ++i) dth[oq + NX + i] = red[NP + NX + i];
+    if (P.status) P.status[c.ocp] = c.status;
+    if (P.pcg_iters) P.pcg_iters[c.ocp] = it;
+  }
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    const long long lb = c.o.lam_off + (long long)k * NX;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      const double v = LP[i * KP + k];
+      if (k == 0) P.dl_dxs[c.o.xs_off + i] = (float)v;   // dl/dx_s = lambda~_0
+      if (P.lamt_out) P.lamt_out[lb + i] = (float)v;
+      if (P.res_lamt) P.res_lamt[lb + i] = v;
+    }
+  }
+}
+
+template <class M, int TEAM>
+__device__ void run_one(const KParams& P, int ocp, float* ws, int lane, int team_in_block) {
+  Ctx<M, TEAM> c;
+  c.P = &P;
+  c.o = P.ocps[ocp];
+  c.ocp = ocp;
+  c.T = c.o.T;
+  c.K = c.o.T + 1;
+  c.dt = c.o.dt;
+  c.L = make_layout(M::NX, M::NU, c.K, TEAM);
+  c.KP = c.L.KP;
+  c.db = reinterpret_cast<double*>(ws);
+  c.fb = ws;
+  c.status = 0;
+  c.tm.lane = lane;
+  c.tm.bar_id = team_in_block + 1;
+  c.tm.red = ws + c.L.red;
+  c.tm.buf = 0;
+  if (P.mode == MODE_VJP) run_backward<M, TEAM>(c);
+  else run_forward<M, TEAM>(c);
+}
+
+template <int TEAM, class... Ms>
+__device__ __forceinline__ void dispatch(const KParams& P, int ocp, float* ws, int lane, int tib) {
+  const OcpRec& o = P.ocps[ocp];
+  bool done = ((o.model == Ms::ID && o.nx == Ms::NX && o.nu == Ms::NU
+                    ? (run_one<Ms, TEAM>(P, ocp, ws, lane, tib), true)
+                    : false) || ...);
+  (void)done;
+}
+
+// One launch processes the work list: team g takes items g, g + G, g + 2G, ... (the list
+// is sorted heaviest first, so this is a longest-processing-time-first assignment).
+template <int TEAM, class... Ms>
+__global__ void __launch_bounds__(256, 2) fused_kernel(const __grid_constant__ KParams P) {
+  extern __shared__ __align__(16) float smem[];
+  const int tib = threadIdx.x / TEAM;
+  const int lane = threadIdx.x % TEAM;
+  const int gteam = blockIdx.x * P.teams_per_block + tib;
+  const int nteams = gridDim.x * P.teams_per_block;
+  float* ws = P.use_gws ? P.gws + (size_t)gteam * P.ws_floats : smem + (size_t)tib * P.ws_floats;
+  for (int w = gteam; w < P.n_work; w += nteams) dispatch<TEAM, Ms...>(P, P.order[w], ws, lane, tib);
+}
+
+}  // namespace dmpc

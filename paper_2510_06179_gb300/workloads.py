@@ -174,17 +174,26 @@ def pendulum_config(B=64, T=40, seed=0, sqp_iters=10, pcg_tol=1e-6, dt=0.05):
 
 
 def bicycle_config(B=64, T=40, seed=0, sqp_iters=10, pcg_tol=1e-6, dt=0.05):
-    """Kinematic bicycle parking to the origin: wheelbase ~ U[2.5, 3.0];
-    x_0: position ~ U[-5, 5]^2, heading ~ U[-pi/2, pi/2], speed ~ U[0, 3]; reference = 0."""
+    """Kinematic bicycle keeping a straight lane at speed: wheelbase ~ U[2.5, 3.0]; reference
+    x_ref,t = (v_ref t dt, 0, 0, v_ref), v_ref ~ U[3, 8] m/s; x_0: lateral offset ~ U[-1, 1] m,
+    heading ~ U[-0.2, 0.2] rad, speed v_ref U[0.8, 1.2]; diag Q ~ U[0.1, 10], Q_T = 10 Q;
+    steering weight ~ U[0.5, 5], acceleration weight ~ U[0.01, 1].  (Cheap steering lets the first
+    QP step from the cold start command angles past +-pi/2, where tan(delta) has poles.)"""
     rng = np.random.default_rng(seed)
     lwb = rng.uniform(2.5, 3.0, size=B)
     q, r, qt = _cost_weights(rng, B, 4, 2)
-    x_s = np.stack([rng.uniform(-5, 5, B), rng.uniform(-5, 5, B),
-                    rng.uniform(-np.pi / 2, np.pi / 2, B), rng.uniform(0, 3, B)], 1)
+    r[:, 0] = rng.uniform(0.5, 5.0, size=B)
+    vref = rng.uniform(3.0, 8.0, size=B)
+    x_s = np.stack([np.zeros(B), rng.uniform(-1, 1, B), rng.uniform(-0.2, 0.2, B),
+                    vref * rng.uniform(0.8, 1.2, B)], 1)
+    tt = np.arange(T + 1) * dt
+    x_ref = np.zeros((B, T + 1, 4))
+    x_ref[:, :, 0] = vref[:, None] * tt[None, :]
+    x_ref[:, :, 3] = vref[:, None]
     th = _pack_theta("kin_bicycle", 4, 2, T, lwb[:, None], None, q, r, qt)
-    return Workload("kin_bicycle", "kin_bicycle", 4, 2, T, dt, _f32(x_s), _f32(th),
-                    _f32(np.zeros((B, T + 1, 4))), sqp_iters=sqp_iters, line_search=True,
-                    pcg_tol=pcg_tol, u_target=_f32(rng.standard_normal((B, 2))))
+    return Workload("kin_bicycle", "kin_bicycle", 4, 2, T, dt, _f32(x_s), _f32(th), _f32(x_ref),
+                    sqp_iters=sqp_iters, line_search=True, pcg_tol=pcg_tol,
+                    u_target=_f32(rng.standard_normal((B, 2))))
 
 
 def sinusoid_reference(rng, B, T, dt, speed):

@@ -1,0 +1,52 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every function
+include/dmpc.h declares; the ctypes binding declares the same names."""
+import ctypes
+import os
+import re
+import subprocess
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "dmpc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dmpc_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("dmpc_create_problem_batch", "dmpc_solve", "dmpc_vjp", "dmpc_destroy"):
+        assert required in names
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2510_06179_gb300 import _lib
+    lib = ctypes.CDLL(_lib.LIB_PATH)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\b(dmpc_[a-z_]+)\b", out))
+    assert set(_declared()) <= exported
+    assert set(_lib.SIGNATURES) == set(_declared())
+
+
+def test_library_reports_version_and_default_options_without_gpu():
+    from paper_2510_06179_gb300 import _lib
+    lib = _lib.load()
+    assert b"sm_103a" in lib.dmpc_version()
+    o = _lib.dmpc_options()
+    lib.dmpc_default_options(ctypes.byref(o))
+    assert o.n_alpha == 5 and abs(o.alpha[4] - 0.01) < 1e-9 and abs(o.ls_eta - 0.4) < 1e-7
+    assert o.sqp_iters == 1 and o.warm_start == 1
+
+
+def test_create_rejects_bad_arguments_before_touching_the_gpu():
+    from paper_2510_06179_gb300 import _lib
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    assert lib.dmpc_create_problem_batch(None, 1, None, None, ctypes.byref(h)) == 1
+    assert h.value is None
+    assert lib.dmpc_vjp(None, None, None, None, None, None, None) == 1
