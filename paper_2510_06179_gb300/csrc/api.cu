@@ -168,7 +168,13 @@ static dmpc_err validate_options(dmpc_handle* h, const dmpc_options& o) {
 static dmpc_err configure_tiling(dmpc_handle* h, int team, int tpb) {
   int maxK = 0;
   for (auto& d : h->descs) maxK = std::max(maxK, d.T + 1);
-  if (team == 0) team = maxK <= 48 ? 32 : (maxK <= 160 ? 64 : (maxK <= 320 ? 128 : 256));
+  int maxnx = 0;
+  for (auto& d : h->descs) maxnx = std::max(maxnx, d.nx);
+  if (team == 0) {
+    // one knot per lane (register-resident PCG) when it fits, else a few knots per lane
+    if (maxnx <= 4 && maxK <= 256) team = maxK <= 32 ? 32 : (maxK <= 64 ? 64 : (maxK <= 128 ? 128 : 256));
+    else team = maxK <= 48 ? 32 : (maxK <= 160 ? 64 : (maxK <= 320 ? 128 : 256));
+  }
   int ws = 0;
   for (auto& d : h->descs) ws = std::max(ws, make_layout(d.nx, d.nu, d.T + 1, team).total_floats);
   const size_t ws_bytes = (size_t)ws * sizeof(float);

@@ -36,7 +36,7 @@ constexpr int kRedMax = 48;     // must equal Team<>::RED_MAX
 struct Layout {
   int KP;
   int d_lam, d_lamp, d_gam, d_wx, d_wu, d_r, d_p, d_y, d_total;  // double arrays (in doubles)
-  int x, u, xp, up, f, C, A, Bm, D, O, Pd, Po, r, p, y, dl, misc, red, f_total;  // floats
+  int x, u, xp, up, f, C, A, Bm, D, O, Pd, Po, r, p, y, dl, misc, red, bnd, f_total;  // floats
   int total_floats;
 };
 
@@ -73,6 +73,7 @@ __host__ __device__ inline Layout make_layout(int nx, int nu, int K, int team) {
   L.dl = f; f += nx * KP;
   L.misc = f; f += kMisc;
   L.red = f; f += 2 * ((team + 31) / 32) * kRedMax;
+  L.bnd = f; f += 2 * 2 * ((team + 31) / 32) * nx;  // warp-boundary exchange, double-buffered
   L.f_total = f;
   L.total_floats = (f + 3) & ~3;
   return L;
@@ -777,6 +778,214 @@ __device__ __noinline__ int stage_pcg(Ctx<M, TEAM>& c) {
   return it;
 }
 
+// Neighbour terms of a block-tridiagonal row for one-knot-per-lane ownership (knot k = lane):
+// vm = v_{k-1} and tn = (M_{k+1})^T v_{k+1}, where every lane provides its own v_k and
+// t_k = M_k^T v_k.  Inside a warp they move by shuffles; across warps lane 31 / lane 0 go through
+// a small shared buffer (double-buffered by `buf`, barrier of the team).
+template <int NX, int TEAM>
+__device__ __forceinline__ void neighbour_terms(const float (&v)[NX], const float (&t)[NX], float (&vm)[NX],
+                                                float (&tn)[NX], Team<TEAM>& tm, float* bnd, int buf) {
+  constexpr int NW = TEAM / 32;
+  const int ln = tm.lane & 31, wid = tm.lane >> 5;
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    vm[i] = __shfl_up_sync(0xffffffffu, v[i], 1);
+    tn[i] = __shfl_down_sync(0xffffffffu, t[i], 1);
+  }
+  if (NW > 1) {
+    float* B = bnd + buf * (NW * 2 * NX);
+    if (ln == 0) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) B[(wid * 2 + 0) * NX + i] = t[i];
+    }
+    if (ln == 31) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) B[(wid * 2 + 1) * NX + i] = v[i];
+    }
+    tm.sync();
+    if (ln == 0) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) vm[i] = wid > 0 ? B[((wid - 1) * 2 + 1) * NX + i] : 0.f;
+    }
+    if (ln == 31) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) tn[i] = wid < NW - 1 ? B[((wid + 1) * 2 + 0) * NX + i] : 0.f;
+    }
+  } else {
+    if (ln == 0) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) vm[i] = 0.f;
+    }
+    if (ln == 31) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) tn[i] = 0.f;
+    }
+  }
+}
+
+// out = Md v + Mo vm + tn, and t = Mo^T v (the part lane k-1 needs), with register blocks.
+template <int NX>
+__device__ __forceinline__ void reg_row(const float (&Md)[NX * NX], const float (&Mo)[NX * NX], const float (&v)[NX],
+                                        float (&t)[NX]) {
+#pragma unroll
+  for (int j = 0; j < NX; ++j) {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) s = fmaf(Mo[i * NX + j], v[i], s);
+    t[j] = s;
+  }
+}
+
+// a4, register-resident variant (one knot per lane, K <= TEAM, nx <= 4): the same algorithm
+// as stage_pcg (FP32 iteration, FP64 solution with reliable updates, FP64 rescue), with the
+// S and Phi^-1 blocks of the lane's knot held in registers for the whole solve and the
+// neighbour coupling done with shuffles, so the inner loop touches no memory.
+template <class M, int TEAM>
+__device__ __noinline__ int stage_pcg_reg(Ctx<M, TEAM>& c) {
+  constexpr int NX = M::NX;
+  const KParams& P = *c.P;
+  const int K = c.K, KP = c.KP;
+  const int k = c.tm.lane;
+  const bool live = k < K;
+  float* R = c.F(c.L.r);
+  float* Y = c.F(c.L.y);
+  float* bnd = c.F(c.L.bnd);
+  double* LP = c.Dp(c.L.d_lamp);
+  const double* G = c.Dp(c.L.d_gam);
+  const float* Pdm = c.F(c.L.Pd);
+  const float* Pom = c.F(c.L.Po);
+  const float tol2 = P.opt.pcg_tol * P.opt.pcg_tol;
+  const float dl2 = P.opt.ru_delta * P.opt.ru_delta;
+  Team<TEAM> tm = c.tm;  // team state in registers for the loop (c lives in local memory)
+  float Dk[NX * NX], Ok[NX * NX], Pdk[NX * NX], Pok[NX * NX];
+#pragma unroll
+  for (int e = 0; e < NX * NX; ++e) {
+    Dk[e] = live ? c.F(c.L.D)[e * KP + k] : 0.f;
+    Ok[e] = (live && k > 0) ? c.F(c.L.O)[e * KP + k] : 0.f;
+    Pdk[e] = live ? Pdm[e * KP + k] : 0.f;
+    Pok[e] = (live && k > 0) ? Pom[e * KP + k] : 0.f;
+  }
+  if (live) {
+#pragma unroll
+    for (int i = 0; i < NX; ++i) Y[i * KP + k] = (float)G[i * KP + k];
+  }
+  hp_residual<M, TEAM>(c, LP);
+  float r[NX], p[NX], dl[NX], rt[NX], t[NX], vm[NX], tn[NX];
+  float red2[2] = {0.f, 0.f};
+  if (live) {
+    float gt[NX];
+    btmv_row<NX>(Pdm, Pom, R, k, K, KP, rt);
+    btmv_row<NX>(Pdm, Pom, Y, k, K, KP, gt);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      r[i] = R[i * KP + k];
+      red2[0] = fmaf(r[i], rt[i], red2[0]);
+      red2[1] = fmaf(Y[i * KP + k], gt[i], red2[1]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { r[i] = 0.f; rt[i] = 0.f; }
+  }
+#pragma unroll
+  for (int i = 0; i < NX; ++i) { p[i] = rt[i]; dl[i] = 0.f; }
+  tm.sum(red2);
+  float eta = red2[0];
+  const float eta0 = red2[1];
+  float eta_ref = eta, eta_true = eta;
+  int it = 0, stall = 0, xb = 0;
+  bool converged = !(eta > tol2 * eta0);
+  const int maxit = P.opt.pcg_max_iters;
+  bool folded = true;
+  while (!converged && it < maxit) {
+    // y = S p
+    reg_row<NX>(Dk, Ok, p, t);
+    neighbour_terms<NX, TEAM>(p, t, vm, tn, tm, bnd, xb); xb ^= 1;
+    float y[NX];
+    float v[1] = {0.f};
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      float s = tn[i];
+#pragma unroll
+      for (int j = 0; j < NX; ++j) s = fmaf(Dk[i * NX + j], p[j], fmaf(Ok[i * NX + j], vm[j], s));
+      y[i] = s;
+      v[0] = fmaf(p[i], s, v[0]);
+    }
+    tm.sum(v);
+    if (!(v[0] > 0.f) || !isfinite(v[0])) break;
+    const float alpha = __fdividef(eta, v[0]);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { dl[i] = fmaf(alpha, p[i], dl[i]); r[i] = fmaf(-alpha, y[i], r[i]); }
+    folded = false;
+    // rt = Phi^-1 r
+    reg_row<NX>(Pdk, Pok, r, t);
+    neighbour_terms<NX, TEAM>(r, t, vm, tn, tm, bnd, xb); xb ^= 1;
+    float e1[1] = {0.f};
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      float s = tn[i];
+#pragma unroll
+      for (int j = 0; j < NX; ++j) s = fmaf(Pdk[i * NX + j], r[j], fmaf(Pok[i * NX + j], vm[j], s));
+      rt[i] = s;
+      e1[0] = fmaf(r[i], s, e1[0]);
+    }
+    tm.sum(e1);
+    float eta_new = e1[0];
+    ++it;
+    if (eta_new < dl2 * eta_ref || !(eta_new > tol2 * eta0) || it >= maxit || !isfinite(eta_new)) {
+      if (live) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) { LP[i * KP + k] += (double)dl[i]; dl[i] = 0.f; }
+      }
+      folded = true;
+      hp_residual<M, TEAM>(c, LP);
+      float e2[1] = {0.f};
+      if (live) {
+        btmv_row<NX>(Pdm, Pom, R, k, K, KP, rt);
+#pragma unroll
+        for (int i = 0; i < NX; ++i) { r[i] = R[i * KP + k]; e2[0] = fmaf(r[i], rt[i], e2[0]); }
+      }
+      tm.sum(e2);
+      eta_new = e2[0];
+      eta_ref = eta_new;
+      if (!(eta_new > tol2 * eta0)) { converged = true; break; }
+      if (!isfinite(eta_new)) break;
+      if (eta_new > 0.25f * eta_true) {
+        if (++stall >= 2) break;
+      } else {
+        stall = 0;
+      }
+      eta_true = eta_new;
+      if (it >= maxit) break;
+    }
+    const float beta = __fdividef(eta_new, eta);
+    eta = eta_new;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) p[i] = fmaf(beta, p[i], rt[i]);
+  }
+  if (!folded) {
+    if (live) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) LP[i * KP + k] += (double)dl[i];
+    }
+    hp_residual<M, TEAM>(c, LP);
+  }
+  c.tm.buf = tm.buf;
+  if (!converged) {
+    c.status |= ST_FP64_RESCUE;
+    it += stage_pcg64<M, TEAM>(c, (double)eta0, maxit);
+  }
+  return it;
+}
+
+// PCG entry: the register-resident inner loop when one knot per lane fits (nx <= 4).
+template <class M, int TEAM>
+__device__ __forceinline__ int run_pcg(Ctx<M, TEAM>& c) {
+  if constexpr (M::NX <= 4) {
+    if (c.K <= TEAM) return stage_pcg_reg<M, TEAM>(c);
+  }
+  return stage_pcg<M, TEAM>(c);
+}
+
 // a5: primal recovery (Eq. 11) from lamp and w = H^T lamp (left by the last hp_residual):
 // x_k = -Q_k^-1 (q_k + w_x,k), u_k = -R^-1 (r_k + w_u,k).  Writes float z+ (xp, up).
 template <class M, int TEAM>
@@ -1009,7 +1218,7 @@ __device__ void run_forward(Ctx<M, TEAM>& c) {
     stage_schur<M, TEAM>(c, true);
     stage_precond<M, TEAM>(c);
     copy_lam_to_lamp<M, TEAM>(c);
-    const int it = stage_pcg<M, TEAM>(c);
+    const int it = run_pcg<M, TEAM>(c);
     stage_recover<M, TEAM>(c);
     if (P.mode == MODE_INSPECT) { write_inspect<M, TEAM>(c, it); break; }
     const float a = stage_linesearch<M, TEAM>(c);
@@ -1107,7 +1316,7 @@ __device__ __noinline__ void run_backward(Ctx<M, TEAM>& c) {
     }
   }
   c.tm.sync();
-  const int it = stage_pcg<M, TEAM>(c);
+  const int it = run_pcg<M, TEAM>(c);
   // z~ = G^-1 (dl/dz - H^T lambda~)  (stored in xp, up)
   const double* WX = c.Dp(c.L.d_wx);
   const double* WU = c.Dp(c.L.d_wu);
@@ -1234,7 +1443,7 @@ __device__ __forceinline__ void dispatch(const KParams& P, int ocp, float* ws, i
 // One launch processes the work list: team g takes items g, g + G, g + 2G, ... (the list
 // is sorted heaviest first, so this is a longest-processing-time-first assignment).
 template <int TEAM, class... Ms>
-__global__ void __launch_bounds__(256, 2) fused_kernel(const __grid_constant__ KParams P) {
+__global__ void __launch_bounds__(256, 1) fused_kernel(const __grid_constant__ KParams P) {
   extern __shared__ __align__(16) float smem[];
   const int tib = threadIdx.x / TEAM;
   const int lane = threadIdx.x % TEAM;
