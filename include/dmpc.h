@@ -138,6 +138,19 @@ dmpc_err dmpc_solve(dmpc_handle* h, const float* x_s, const float* theta, const 
 dmpc_err dmpc_vjp(dmpc_handle* h, const float* dl_dz, float* dl_dtheta, float* dl_dxs, float* lamt_out,
                   int* status_out, int* pcg_iters_out);
 
+/* The plain one-launch-per-step form of the same method, for comparison: identical arguments,
+ * results and resident state as dmpc_solve / dmpc_vjp (they may be mixed on one handle), but
+ * every step (linearise, Schur blocks, preconditioner, each PCG operation of Algorithm 4,
+ * recovery, line search) is a separate kernel launch over the batch, the per-OCP workspace
+ * (the S and Phi^-1 blocks included) lives in HBM, and the host polls PCG convergence every
+ * 8 iterations (a device-to-host copy and a stream synchronisation).  Blocking: returns after
+ * the last poll; the final launches are asynchronous.  Stored-Schur mode is not used. */
+dmpc_err dmpc_solve_plain(dmpc_handle* h, const float* x_s, const float* theta, const float* x_ref,
+                          const float* z_init, const float* lam_init, float* z_out, float* lam_out,
+                          int* status_out, int* pcg_iters_out, float* alpha_out);
+dmpc_err dmpc_vjp_plain(dmpc_handle* h, const float* dl_dz, float* dl_dtheta, float* dl_dxs, float* lamt_out,
+                        int* status_out, int* pcg_iters_out);
+
 /* Diagnostic: build and solve ONE QP at (z, lam) for every OCP (Eq. 4, 8-11, Algorithm 4)
  * and write a record per OCP at record + rec_off[b] (rec_off from dmpc_inspect_offsets):
  *   A_t (T nx nx), B_t (T nx nu), C_t (T nx), g (K nx: x_0 - x_s, f_0..f_{T-1}),

@@ -31,6 +31,8 @@ SIGNATURES = {
     "dmpc_layout": (c_int, [P, P, P, P, P, P]),
     "dmpc_solve": (c_int, [P, P, P, P, P, P, P, P, P, P, P]),
     "dmpc_vjp": (c_int, [P, P, P, P, P, P, P]),
+    "dmpc_solve_plain": (c_int, [P, P, P, P, P, P, P, P, P, P, P]),
+    "dmpc_vjp_plain": (c_int, [P, P, P, P, P, P, P]),
     "dmpc_qp_inspect": (c_int, [P, P, P, P, P, P, P]),
     "dmpc_inspect_offsets": (c_int, [P, P]),
     "dmpc_set_stream": (c_int, [P, P]),

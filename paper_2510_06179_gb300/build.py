@@ -13,7 +13,9 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libdmpc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+TEAMS = (32, 64, 128, 256)
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "177",
+         "-I", os.path.join(ROOT, "include")]
 
 
 def _nvcc():
@@ -42,10 +44,19 @@ def build(verbose=False, jobs=None, extra=()):
     cmds, objs = [], []
     for s in _sources():
         src = os.path.join(CSRC, s)
-        obj = os.path.join(OUT, s[:-3] + ".o")
-        objs.append(obj)
-        if _stale(obj, [src] + headers):
-            cmds.append([nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj])
+        # kernel units (k_*.cu) are compiled once per team size: more, smaller units in parallel
+        variants = [(f"_t{t}", [f"-DDMPC_TEAM={t}"]) for t in TEAMS] if s.startswith("k_") else [("", [])]
+        for suffix, defs in variants:
+            obj = os.path.join(OUT, s[:-3] + suffix + ".o")
+            objs.append(obj)
+            if _stale(obj, [src] + headers):
+                cmds.append([nvcc, *ARCH, *FLAGS, *defs, *extra, "-c", src, "-o", obj])
+    # longest units first (rigid body, mixed, LQ) so the pool finishes early
+    weight = lambda c: (2 if any(k in c[-3] for k in ("rigid", "mixed", "lq", "single")) else 1)
+    cmds.sort(key=weight, reverse=True)
+    for f in os.listdir(OUT):
+        if f.endswith(".o") and os.path.join(OUT, f) not in objs:
+            os.remove(os.path.join(OUT, f))
     jobs = jobs or max(1, min(len(cmds), os.cpu_count() or 4))
 
     def run(cmd):

@@ -13,9 +13,25 @@
 
 #include "../../include/dmpc.h"
 #include "fused.cuh"
+#include "plain.cuh"
 #include "launch.h"
 
 using namespace dmpc;
+
+namespace dmpc {
+__global__ void plain_count_active(const PlainState* st, int n, int* out) {
+  __shared__ int part[256];
+  int acc = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += st[i].active;
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = part[0];
+}
+}  // namespace dmpc
 
 namespace {
 
@@ -50,16 +66,8 @@ std::string g_create_error;
 const std::vector<KernelEntry>& registry() {
   std::lock_guard<std::mutex> lk(g_reg_mu);
   if (g_registry.empty()) {
-    KernelEntry buf[128];
-    int n = 0;
-    n += register_lq(buf + n);
-    n += register_pendulum(buf + n);
-    n += register_cartpole(buf + n);
-    n += register_bicycle(buf + n);
-    n += register_single_track(buf + n);
-    n += register_rigid_body(buf + n);
-    n += register_attitude(buf + n);
-    n += register_mixed(buf + n);
+    KernelEntry buf[kMaxKernelEntries];
+    int n = collect_kernel_entries(buf);
     g_registry.assign(buf, buf + n);
   }
   return g_registry;
@@ -101,6 +109,13 @@ struct dmpc_handle {
   bool use_gws = false;
   size_t smem = 0;
   LaunchFn fn = nullptr;
+  PlainFn plain_fn = nullptr;
+  // plain one-launch-per-step form (allocated on first use)
+  float* plain_ws = nullptr;
+  PlainState* plain_st = nullptr;
+  int* plain_dcount = nullptr;
+  int* plain_hcount = nullptr;
+  int plain_ws_floats = 0;
   std::string err;
 };
 
@@ -189,16 +204,17 @@ static dmpc_err configure_tiling(dmpc_handle* h, int team, int tpb) {
   if (tpb < 1) tpb = 1;
   // find the kernel
   LaunchFn fn = nullptr;
+  PlainFn pfn = nullptr;
   for (auto& e : registry()) {
     if (e.team != team) continue;
-    if (h->uniform && e.model == h->model0 && e.nx == h->nx0 && e.nu == h->nu0) { fn = e.fn; break; }
+    if (h->uniform && e.model == h->model0 && e.nx == h->nx0 && e.nu == h->nu0) { fn = e.fn; pfn = e.plain; break; }
   }
   if (!fn) {
     bool has_lq = false;
     for (auto& d : h->descs) has_lq |= d.model == DMPC_MODEL_LQ;
     if (has_lq) return fail(h, DMPC_E_UNSUPPORTED, "LQ OCPs cannot be mixed with other models in one batch");
     for (auto& e : registry())
-      if (e.model == -1 && e.team == team) { fn = e.fn; break; }
+      if (e.model == -1 && e.team == team) { fn = e.fn; pfn = e.plain; break; }
   }
   if (!fn) return fail(h, DMPC_E_UNSUPPORTED, "no kernel for this model / team size");
   int grid = (h->batch + tpb - 1) / tpb;
@@ -219,6 +235,7 @@ static dmpc_err configure_tiling(dmpc_handle* h, int team, int tpb) {
   h->max_ws_floats = ws;
   h->smem = h->use_gws ? 0 : (size_t)tpb * ws_bytes;
   h->fn = fn;
+  h->plain_fn = pfn;
   return DMPC_OK;
 }
 
@@ -447,6 +464,137 @@ extern "C" dmpc_err dmpc_qp_inspect(dmpc_handle* h, const float* x_s, const floa
   return launch(h, P);
 }
 
+// ---------------------------------------------------------------------------------------
+// Plain one-launch-per-step form (the comparator of the fused kernel): the same stages, one
+// launch per step over the batch, per-OCP workspace in HBM, convergence polled by the host
+// every kPlainPoll PCG iterations.
+static const int kPlainPoll = 8;
+
+static dmpc_err plain_prepare(dmpc_handle* h, KParams* P) {
+  const int team = h->team;
+  int ws = 0;
+  for (auto& d : h->descs) ws = std::max(ws, make_layout(d.nx, d.nu, d.T + 1, team).total_floats);
+  if (!h->plain_ws || ws != h->plain_ws_floats) {
+    cudaFree(h->plain_ws);
+    h->plain_ws = nullptr;
+    if (cudaMalloc(&h->plain_ws, (size_t)ws * h->batch * sizeof(float)) != cudaSuccess)
+      return fail(h, DMPC_E_OOM, "plain-form workspace allocation failed");
+    h->plain_ws_floats = ws;
+  }
+  if (!h->plain_st) {
+    if (cudaMalloc(&h->plain_st, sizeof(PlainState) * h->batch) != cudaSuccess ||
+        cudaMalloc(&h->plain_dcount, sizeof(int)) != cudaSuccess ||
+        cudaHostAlloc(&h->plain_hcount, sizeof(int), cudaHostAllocDefault) != cudaSuccess)
+      return fail(h, DMPC_E_OOM, "plain-form state allocation failed");
+    cudaMemsetAsync(h->plain_st, 0, sizeof(PlainState) * h->batch, h->stream);
+  }
+  if (!h->plain_fn) return fail(h, DMPC_E_UNSUPPORTED, "no plain-form kernel for this batch");
+  P->gws = h->plain_ws;
+  P->use_gws = 1;
+  P->ws_floats = ws;
+  P->teams_per_block = 1;
+  return DMPC_OK;
+}
+
+static dmpc_err plain_pcg(dmpc_handle* h, const KParams& P) {
+  auto L = [&](int step) { return h->plain_fn(P, h->plain_st, step, 0, h->batch, h->team, h->stream); };
+  const int maxit = h->opt.pcg_max_iters;
+  for (int base = 0; base < maxit; base += kPlainPoll) {
+    for (int j = 0; j < kPlainPoll; ++j) {
+      if (L(PS_MATVEC) != cudaSuccess || L(PS_AXPY) != cudaSuccess || L(PS_PRECAPPLY) != cudaSuccess ||
+          L(PS_BETA) != cudaSuccess)
+        return fail(h, DMPC_E_CUDA, "plain PCG launch failed");
+    }
+    plain_count_active<<<1, 256, 0, h->stream>>>(h->plain_st, h->batch, h->plain_dcount);
+    cudaMemcpyAsync(h->plain_hcount, h->plain_dcount, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "plain PCG poll");
+    if (*h->plain_hcount == 0) break;
+  }
+  return DMPC_OK;
+}
+
+extern "C" dmpc_err dmpc_solve_plain(dmpc_handle* h, const float* x_s, const float* theta, const float* x_ref,
+                                     const float* z_init, const float* lam_init, float* z_out, float* lam_out,
+                                     int* status_out, int* pcg_iters_out, float* alpha_out) {
+  if (!h) return DMPC_E_ARG;
+  REQUIRE_DEV(x_s, "x_s");
+  REQUIRE_DEV(theta, "theta");
+  REQUIRE_DEV(z_out, "z_out");
+  OPTIONAL_DEV(x_ref, "x_ref");
+  OPTIONAL_DEV(z_init, "z_init");
+  OPTIONAL_DEV(lam_init, "lam_init");
+  OPTIONAL_DEV(lam_out, "lam_out");
+  OPTIONAL_DEV(status_out, "status_out");
+  OPTIONAL_DEV(pcg_iters_out, "pcg_iters_out");
+  OPTIONAL_DEV(alpha_out, "alpha_out");
+  KParams P = base_params(h);
+  dmpc_err er = plain_prepare(h, &P);
+  if (er != DMPC_OK) return er;
+  P.mode = MODE_SOLVE;
+  P.x_s = x_s; P.theta = theta; P.x_ref = x_ref;
+  const bool warm = h->opt.warm_start && h->have_solution;
+  P.z_init = z_init ? z_init : (warm ? h->res_z : nullptr);
+  P.lam_init_f = lam_init;
+  P.lam_init_d = (!lam_init && warm) ? h->res_lam : nullptr;
+  P.z_out = z_out; P.lam_out = lam_out;
+  P.res_z = h->res_z; P.res_lam = h->res_lam;
+  P.res_xs = h->res_xs; P.res_th = h->res_th; P.res_xref = h->res_xref;
+  P.status = status_out; P.pcg_iters = pcg_iters_out; P.alpha_hist = alpha_out;
+  auto L = [&](int step, int s) { return h->plain_fn(P, h->plain_st, step, s, h->batch, h->team, h->stream); };
+  if (L(PS_LOAD, 0) != cudaSuccess) return fail(h, DMPC_E_CUDA, "plain launch failed");
+  for (int s = 0; s < h->opt.sqp_iters; ++s) {
+    if (L(PS_LIN, s) != cudaSuccess || L(PS_SCHUR, s) != cudaSuccess || L(PS_PREC, s) != cudaSuccess ||
+        L(PS_PCG_SETUP, s) != cudaSuccess)
+      return fail(h, DMPC_E_CUDA, "plain launch failed");
+    er = plain_pcg(h, P);
+    if (er != DMPC_OK) return er;
+    if (L(PS_PCG_FINISH, s) != cudaSuccess || L(PS_RECOVER, s) != cudaSuccess || L(PS_LS, s) != cudaSuccess)
+      return fail(h, DMPC_E_CUDA, "plain launch failed");
+  }
+  if (L(PS_FWD_OUT, 0) != cudaSuccess) return fail(h, DMPC_E_CUDA, "plain launch failed");
+  h->have_solution = true;
+  h->have_store = false;
+  h->last_had_xref = x_ref != nullptr;
+  return DMPC_OK;
+}
+
+extern "C" dmpc_err dmpc_vjp_plain(dmpc_handle* h, const float* dl_dz, float* dl_dtheta, float* dl_dxs,
+                                   float* lamt_out, int* status_out, int* pcg_iters_out) {
+  if (!h) return DMPC_E_ARG;
+  if (!h->have_solution) return fail(h, DMPC_E_STATE, "dmpc_vjp_plain called before any solve on this handle");
+  REQUIRE_DEV(dl_dz, "dl_dz");
+  REQUIRE_DEV(dl_dtheta, "dl_dtheta");
+  REQUIRE_DEV(dl_dxs, "dl_dxs");
+  OPTIONAL_DEV(lamt_out, "lamt_out");
+  OPTIONAL_DEV(status_out, "status_out");
+  OPTIONAL_DEV(pcg_iters_out, "pcg_iters_out");
+  KParams P = base_params(h);
+  dmpc_err er = plain_prepare(h, &P);
+  if (er != DMPC_OK) return er;
+  P.mode = MODE_VJP;
+  P.x_s = h->res_xs; P.theta = h->res_th; P.x_ref = h->last_had_xref ? h->res_xref : nullptr;
+  P.z_init = h->res_z;
+  P.lam_init_d = h->res_lam;
+  P.dl_dz = dl_dz;
+  P.lamt_init = (h->opt.warm_start && h->have_lamt) ? h->res_lamt : nullptr;
+  P.res_lamt = h->res_lamt;
+  P.dl_dtheta = dl_dtheta; P.dl_dxs = dl_dxs; P.lamt_out = lamt_out;
+  P.status = status_out; P.pcg_iters = nullptr;
+  auto L = [&](int step) { return h->plain_fn(P, h->plain_st, step, 0, h->batch, h->team, h->stream); };
+  if (L(PS_LOAD) != cudaSuccess || L(PS_LIN) != cudaSuccess || L(PS_SCHUR) != cudaSuccess ||
+      L(PS_PREC) != cudaSuccess || L(PS_PCG_SETUP) != cudaSuccess)
+    return fail(h, DMPC_E_CUDA, "plain launch failed");
+  er = plain_pcg(h, P);
+  if (er != DMPC_OK) return er;
+  P.pcg_iters = pcg_iters_out;
+  auto L2 = [&](int step) { return h->plain_fn(P, h->plain_st, step, 0, h->batch, h->team, h->stream); };
+  if (L2(PS_PCG_FINISH) != cudaSuccess || L2(PS_BWD_FINISH) != cudaSuccess)
+    return fail(h, DMPC_E_CUDA, "plain launch failed");
+  h->have_lamt = true;
+  return DMPC_OK;
+}
+
 extern "C" dmpc_err dmpc_set_stream(dmpc_handle* h, void* s) {
   if (!h) return DMPC_E_ARG;
   h->stream = (cudaStream_t)s;
@@ -486,6 +634,10 @@ extern "C" void dmpc_destroy(dmpc_handle* h) {
   cudaFree(h->res_xref);
   cudaFree(h->store);
   cudaFree(h->gws);
+  cudaFree(h->plain_ws);
+  cudaFree(h->plain_st);
+  cudaFree(h->plain_dcount);
+  if (h->plain_hcount) cudaFreeHost(h->plain_hcount);
   delete h;
 }
 

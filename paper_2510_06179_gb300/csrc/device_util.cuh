@@ -258,6 +258,20 @@ struct Team {
     buf ^= 1;
   }
 
+  // Bitwise OR of an int over the team (status flags); every thread receives the result.
+  __device__ __forceinline__ int bor(int v) {
+    v = __reduce_or_sync(0xffffffffu, (unsigned)v);
+    if (TEAM <= 32) return v;
+    float* rb = red + buf * (NW * RED_MAX);
+    int w = lane >> 5;
+    if ((lane & 31) == 0) reinterpret_cast<int*>(rb)[w] = v;
+    sync();
+    int o = 0;
+    for (int q = 0; q < NW; ++q) o |= reinterpret_cast<int*>(rb)[q];
+    buf ^= 1;
+    return o;
+  }
+
   // double-precision variant (each double takes two float slots of the scratch).
   template <int NV>
   __device__ __forceinline__ void sum(double (&v)[NV]) {

@@ -30,7 +30,7 @@ enum StatusBits : int {
   ST_PCG_BREAKDOWN = 16, ST_CHOL_FAIL = 32, ST_FP64_RESCUE = 64
 };
 
-constexpr int kMisc = 128;      // per-team scalars (theta, cost weights)
+constexpr int kMisc = 256;      // per-team scalars (theta, cost weights, reciprocals)
 constexpr int kRedMax = 48;     // must equal Team<>::RED_MAX
 
 struct Layout {
@@ -83,6 +83,9 @@ __host__ __device__ inline Layout make_layout(int nx, int nu, int K, int team) {
 // [64,80) projected Q, [80,96) projected R, [96,112) projected Q_T
 constexpr int MS_TH = 0, MS_Q = 16, MS_R = 32, MS_QT = 48, MS_QP = 64, MS_RP = 80, MS_QTP = 96;
 constexpr int MS_BAD = 120;  // nonzero when a weight or parameter is not finite
+// double reciprocals of the projected weights (float offset 128, 8-byte aligned):
+// [0,16) 1/Q, [16,24) 1/R, [24,40) 1/Q_T  (in doubles)
+constexpr int MS_DINV = 128;
 
 template <class M, int TEAM>
 struct Ctx {
@@ -102,6 +105,12 @@ struct Ctx {
   __device__ __forceinline__ float misc(int i) const { return fb[L.misc + i]; }
   __device__ __forceinline__ float qraw(int k, int i) const { return misc((k < T ? MS_Q : MS_QT) + i); }
   __device__ __forceinline__ float qproj(int k, int i) const { return misc((k < T ? MS_QP : MS_QTP) + i); }
+  __device__ __forceinline__ double qinv(int k, int i) const {
+    return reinterpret_cast<const double*>(fb + L.misc + MS_DINV)[(k < T ? 0 : 24) + i];
+  }
+  __device__ __forceinline__ double rinv(int i) const {
+    return reinterpret_cast<const double*>(fb + L.misc + MS_DINV)[16 + i];
+  }
   __device__ __forceinline__ float xref(int k, int i) const {
     return P->x_ref ? __ldg(P->x_ref + o.xref_off + (long long)k * NX + i) : 0.f;
   }
@@ -156,54 +165,54 @@ __device__ __forceinline__ void btmv_row(const float* Md, const float* Mo, const
 template <int NX>
 __device__ bool spd_inverse(const float* a, float* inv) {
   float L[NX * NX];
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
   for (int i = 0; i < NX * NX; ++i) L[i] = 0.f;
   bool ok = true;
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
   for (int j = 0; j < NX; ++j) {
     float s = a[j * NX + j];
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
     for (int k = 0; k < j; ++k) s -= L[j * NX + k] * L[j * NX + k];
     if (!(s > 0.f)) { ok = false; s = fabsf(a[j * NX + j]) + 1e-30f; }
     float d = sqrtf(s);
     L[j * NX + j] = d;
     float id = 1.f / d;
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = j + 1; i < NX; ++i) {
       float t = a[i * NX + j];
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
       for (int k = 0; k < j; ++k) t -= L[i * NX + k] * L[j * NX + k];
       L[i * NX + j] = t * id;
     }
   }
   if (!ok) {
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = 0; i < NX * NX; ++i) inv[i] = 0.f;
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = 0; i < NX; ++i) inv[i * NX + i] = 1.f / (fabsf(a[i * NX + i]) + 1e-30f);
     return false;
   }
   // W = L^-1 (lower triangular), forward substitution column by column
   float W[NX * NX];
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
   for (int i = 0; i < NX * NX; ++i) W[i] = 0.f;
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
   for (int c = 0; c < NX; ++c) {
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = c; i < NX; ++i) {
       float t = (i == c) ? 1.f : 0.f;
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
       for (int k = c; k < i; ++k) t -= L[i * NX + k] * W[k * NX + c];
       W[i * NX + c] = t / L[i * NX + i];
     }
   }
   // inv = W^T W
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
   for (int i = 0; i < NX; ++i) {
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
     for (int j = 0; j <= i; ++j) {
       float s = 0.f;
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
       for (int k = (i > j ? i : j); k < NX; ++k) s += W[k * NX + i] * W[k * NX + j];
       inv[i * NX + j] = s;
       inv[j * NX + i] = s;
@@ -238,6 +247,9 @@ __device__ __noinline__ void stage_load(Ctx<M, TEAM>& c, bool use_z_init) {
     for (int i = 0; i < NX; ++i) { ms[MS_QTP + i] = fmaxf(ms[MS_QT + i], fqt); bad |= !isfinite(ms[MS_QT + i]); }
     for (int i = 0; i < M::NP; ++i) bad |= !isfinite(ms[MS_TH + i]);
     ms[MS_BAD] = bad ? 1.f : 0.f;
+    double* dinv = reinterpret_cast<double*>(ms + MS_DINV);
+    for (int i = 0; i < NX; ++i) { dinv[i] = 1.0 / (double)ms[MS_QP + i]; dinv[24 + i] = 1.0 / (double)ms[MS_QTP + i]; }
+    for (int i = 0; i < NU; ++i) dinv[16 + i] = 1.0 / (double)ms[MS_RP + i];
   }
   const float* xs = P.x_s + c.o.xs_off;
   if (P.mode == MODE_SOLVE && P.res_th) {
@@ -389,58 +401,58 @@ __device__ __noinline__ void stage_schur(Ctx<M, TEAM>& c, bool rhs_from_qp) {
   const float* xs = P.x_s + c.o.xs_off;
   for (int k = c.tm.lane; k < K; k += TEAM) {
     float qi[NX];
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = 0; i < NX; ++i) qi[i] = 1.f / c.qproj(k, i);
     if (k == 0) {
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
       for (int i = 0; i < NX; ++i)
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
         for (int j = 0; j < NX; ++j) D[(i * NX + j) * KP] = (i == j) ? qi[i] : 0.f;
       if (rhs_from_qp) {
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
         for (int i = 0; i < NX; ++i)
-          G[i * KP] = -(double)xs[i] - c.qlin(0, i, X[i * KP]) / (double)c.qproj(0, i);
+          G[i * KP] = -(double)xs[i] - c.qlin(0, i, X[i * KP]) * c.qinv(0, i);
       }
       continue;
     }
     const int t = k - 1;
     float qt[NX], ri[NU];
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = 0; i < NX; ++i) qt[i] = 1.f / c.qproj(t, i);
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = 0; i < NU; ++i) ri[i] = 1.f / c.misc(MS_RP + i);
     float a[NX * NX], b[NX * NU];
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = 0; i < NX * NX; ++i) a[i] = A[i * KP + k];
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = 0; i < NX * NU; ++i) b[i] = Bm[i * KP + k];
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = 0; i < NX; ++i) {
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
       for (int j = 0; j <= i; ++j) {
         float s = (i == j) ? qi[i] : 0.f;
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
         for (int l = 0; l < NX; ++l) s = fmaf(a[i * NX + l] * qt[l], a[j * NX + l], s);
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
         for (int l = 0; l < NU; ++l) s = fmaf(b[i * NU + l] * ri[l], b[j * NU + l], s);
         D[(i * NX + j) * KP + k] = s;
         D[(j * NX + i) * KP + k] = s;
       }
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
       for (int j = 0; j < NX; ++j) O[(i * NX + j) * KP + k] = a[i * NX + j] * qt[j];
     }
     if (rhs_from_qp) {
       double vq[NX], vr[NU];
-#pragma unroll
-      for (int j = 0; j < NX; ++j) vq[j] = c.qlin(t, j, X[j * KP + t]) / (double)c.qproj(t, j);
-#pragma unroll
-      for (int j = 0; j < NU; ++j) vr[j] = c.rlin(j, U[j * KP + t]) / (double)c.misc(MS_RP + j);
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
+      for (int j = 0; j < NX; ++j) vq[j] = c.qlin(t, j, X[j * KP + t]) * c.qinv(t, j);
+#pragma unroll (NX <= 6 ? 32 : 1)
+      for (int j = 0; j < NU; ++j) vr[j] = c.rlin(j, U[j * KP + t]) * c.rinv(j);
+#pragma unroll (NX <= 6 ? 32 : 1)
       for (int i = 0; i < NX; ++i) {
-        double z = c.qlin(k, i, X[i * KP + k]) / (double)c.qproj(k, i);
-#pragma unroll
+        double z = c.qlin(k, i, X[i * KP + k]) * c.qinv(k, i);
+#pragma unroll (NX <= 6 ? 32 : 1)
         for (int j = 0; j < NX; ++j) z += (double)a[i * NX + j] * vq[j];
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
         for (int j = 0; j < NU; ++j) z += (double)b[i * NU + j] * vr[j];
         G[i * KP + k] = -(double)C[i * KP + k] - z;
       }
@@ -460,10 +472,10 @@ __device__ __noinline__ void stage_precond(Ctx<M, TEAM>& c) {
   float* Po = c.F(c.L.Po);
   for (int k = c.tm.lane; k < K; k += TEAM) {
     float a[NX * NX], inv[NX * NX];
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = 0; i < NX * NX; ++i) a[i] = D[i * KP + k];
     if (!spd_inverse<NX>(a, inv)) c.status |= ST_CHOL_FAIL;
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = 0; i < NX * NX; ++i) Pd[i * KP + k] = inv[i];
   }
   c.tm.sync();
@@ -471,21 +483,21 @@ __device__ __noinline__ void stage_precond(Ctx<M, TEAM>& c) {
     if (k == 0) continue;
     float t1[NX * NX];
     // t1 = O_k Pd_{k-1}
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = 0; i < NX; ++i)
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
       for (int j = 0; j < NX; ++j) {
         float s = 0.f;
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
         for (int l = 0; l < NX; ++l) s = fmaf(O[(i * NX + l) * KP + k], Pd[(l * NX + j) * KP + k - 1], s);
         t1[i * NX + j] = s;
       }
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = 0; i < NX; ++i)
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
       for (int j = 0; j < NX; ++j) {
         float s = 0.f;
-#pragma unroll
+#pragma unroll (NX <= 6 ? 32 : 1)
         for (int l = 0; l < NX; ++l) s = fmaf(Pd[(i * NX + l) * KP + k], t1[l * NX + j], s);
         Po[(i * NX + j) * KP + k] = -s;
       }
@@ -539,14 +551,14 @@ __device__ __noinline__ void hp_apply(Ctx<M, TEAM>& c, const double* src, bool r
   for (int k = c.tm.lane; k < K; k += TEAM) {
     double s[NX];
 #pragma unroll
-    for (int i = 0; i < NX; ++i) s[i] = WX[i * KP + k] / (double)c.qproj(k, i);
+    for (int i = 0; i < NX; ++i) s[i] = WX[i * KP + k] * c.qinv(k, i);
     if (k > 0) {
       const int t = k - 1;
       double vx[NX], vu[NU];
 #pragma unroll
-      for (int j = 0; j < NX; ++j) vx[j] = WX[j * KP + t] / (double)c.qproj(t, j);
+      for (int j = 0; j < NX; ++j) vx[j] = WX[j * KP + t] * c.qinv(t, j);
 #pragma unroll
-      for (int j = 0; j < NU; ++j) vu[j] = WU[j * KP + t] / (double)c.misc(MS_RP + j);
+      for (int j = 0; j < NU; ++j) vu[j] = WU[j * KP + t] * c.rinv(j);
 #pragma unroll
       for (int i = 0; i < NX; ++i) {
         double acc = s[i];
@@ -589,17 +601,21 @@ __device__ __noinline__ int stage_pcg64(Ctx<M, TEAM>& c, double eta0, int maxit)
   double* Y = c.Dp(c.L.d_y);
   const double* G = c.Dp(c.L.d_gam);
   const double tol2 = (double)P.opt.pcg_tol * (double)P.opt.pcg_tol;
+  float* Rf = c.F(c.L.r);  // FP32 copy of the residual for the (FP32) preconditioner
   hp_apply<M, TEAM>(c, LP, false, Y);
   for (int k = c.tm.lane; k < K; k += TEAM)
 #pragma unroll
-    for (int i = 0; i < NX; ++i) Rv[i * KP + k] = G[i * KP + k] - Y[i * KP + k];
+    for (int i = 0; i < NX; ++i) {
+      Rv[i * KP + k] = G[i * KP + k] - Y[i * KP + k];
+      Rf[i * KP + k] = (float)Rv[i * KP + k];
+    }
   c.tm.sync();
   double e[1] = {0.0};
   for (int k = c.tm.lane; k < K; k += TEAM) {
-    double z[NX];
-    btmv_row<NX, double>(Pd, Po, Rv, k, K, KP, z);
+    float z[NX];
+    btmv_row<NX>(Pd, Po, Rf, k, K, KP, z);
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { Pv[i * KP + k] = z[i]; e[0] += Rv[i * KP + k] * z[i]; }
+    for (int i = 0; i < NX; ++i) { Pv[i * KP + k] = (double)z[i]; e[0] += Rv[i * KP + k] * (double)z[i]; }
   }
   c.tm.sum(e);
   double eta = e[0];
@@ -619,14 +635,15 @@ __device__ __noinline__ int stage_pcg64(Ctx<M, TEAM>& c, double eta0, int maxit)
       for (int i = 0; i < NX; ++i) {
         LP[i * KP + k] += alpha * Pv[i * KP + k];
         Rv[i * KP + k] -= alpha * Y[i * KP + k];
+        Rf[i * KP + k] = (float)Rv[i * KP + k];
       }
     c.tm.sync();
     double e1[1] = {0.0};
     for (int k = c.tm.lane; k < K; k += TEAM) {
-      double z[NX];
-      btmv_row<NX, double>(Pd, Po, Rv, k, K, KP, z);
+      float z[NX];
+      btmv_row<NX>(Pd, Po, Rf, k, K, KP, z);
 #pragma unroll
-      for (int i = 0; i < NX; ++i) { Y[i * KP + k] = z[i]; e1[0] += Rv[i * KP + k] * z[i]; }
+      for (int i = 0; i < NX; ++i) { Y[i * KP + k] = (double)z[i]; e1[0] += Rv[i * KP + k] * (double)z[i]; }
     }
     c.tm.sum(e1);
     ++it;
@@ -1001,11 +1018,11 @@ __device__ __noinline__ void stage_recover(Ctx<M, TEAM>& c) {
   for (int k = c.tm.lane; k < K; k += TEAM) {
 #pragma unroll
     for (int i = 0; i < NX; ++i)
-      XP[i * KP + k] = (float)(-(c.qlin(k, i, X[i * KP + k]) + WX[i * KP + k]) / (double)c.qproj(k, i));
+      XP[i * KP + k] = (float)(-(c.qlin(k, i, X[i * KP + k]) + WX[i * KP + k]) * c.qinv(k, i));
     if (k < T) {
 #pragma unroll
       for (int i = 0; i < NU; ++i)
-        UP[i * KP + k] = (float)(-(c.rlin(i, U[i * KP + k]) + WU[i * KP + k]) / (double)c.misc(MS_RP + i));
+        UP[i * KP + k] = (float)(-(c.rlin(i, U[i * KP + k]) + WU[i * KP + k]) * c.rinv(i));
     }
   }
   c.tm.sync();
@@ -1204,30 +1221,13 @@ __device__ __noinline__ void write_inspect(Ctx<M, TEAM>& c, int iters) {
   }
 }
 
-// ---------------------------------------------------------------------------------------
-// Forward: the SQP iterations of one OCP (or one QP in inspect mode).
+// Forward outputs: optional stored blocks at the returned z, then z, lambda, the resident
+// warm-start copies and the status.
 template <class M, int TEAM>
-__device__ void run_forward(Ctx<M, TEAM>& c) {
+__device__ __noinline__ void stage_fwd_outputs(Ctx<M, TEAM>& c) {
   constexpr int NX = M::NX, NU = M::NU, NZ = NX + NU;
   const KParams& P = *c.P;
   const int T = c.T, K = c.K, KP = c.KP;
-  stage_load<M, TEAM>(c, P.z_init != nullptr);
-  const int iters = (P.mode == MODE_INSPECT) ? 1 : P.opt.sqp_iters;
-  for (int s = 0; s < iters; ++s) {
-    stage_linearise<M, TEAM>(c);
-    stage_schur<M, TEAM>(c, true);
-    stage_precond<M, TEAM>(c);
-    copy_lam_to_lamp<M, TEAM>(c);
-    const int it = run_pcg<M, TEAM>(c);
-    stage_recover<M, TEAM>(c);
-    if (P.mode == MODE_INSPECT) { write_inspect<M, TEAM>(c, it); break; }
-    const float a = stage_linesearch<M, TEAM>(c);
-    if (c.tm.lane == 0) {
-      if (P.pcg_iters) P.pcg_iters[(long long)c.ocp * P.opt.sqp_iters + s] = it;
-      if (P.alpha_hist) P.alpha_hist[(long long)c.ocp * P.opt.sqp_iters + s] = a;
-    }
-  }
-  if (P.mode == MODE_INSPECT) return;
   if (P.store_mode && P.store) {
     // stored-Schur mode: re-linearise at the returned z and keep the blocks for the vjp
     stage_linearise<M, TEAM>(c);
@@ -1263,27 +1263,45 @@ __device__ void run_forward(Ctx<M, TEAM>& c) {
       }
     }
   }
-  float fb[1] = {(float)bad};
-  c.tm.sum(fb);
-  if (fb[0] > 0.f) c.status |= ST_NONFINITE;
+  if (bad) c.status |= ST_NONFINITE;
+  c.status = c.tm.bor(c.status);
   if (c.tm.lane == 0 && P.status) P.status[c.ocp] = c.status;
 }
 
-// Backward (Algorithm 3): adjoint PCG with the same S, z~, and the theta contraction.
+// ---------------------------------------------------------------------------------------
+// Forward: the SQP iterations of one OCP (or one QP in inspect mode).
 template <class M, int TEAM>
-__device__ __noinline__ void run_backward(Ctx<M, TEAM>& c) {
-  constexpr int NX = M::NX, NU = M::NU, NZ = NX + NU, NP = M::NP;
+__device__ void run_forward(Ctx<M, TEAM>& c) {
+  constexpr int NX = M::NX, NU = M::NU, NZ = NX + NU;
   const KParams& P = *c.P;
   const int T = c.T, K = c.K, KP = c.KP;
-  stage_load<M, TEAM>(c, true);   // z (returned solution) and lambda (forward multipliers)
-  if (P.store_mode && P.store) {
-    store_blocks<M, TEAM>(c, true);
-  } else {
+  stage_load<M, TEAM>(c, P.z_init != nullptr);
+  const int iters = (P.mode == MODE_INSPECT) ? 1 : P.opt.sqp_iters;
+  for (int s = 0; s < iters; ++s) {
     stage_linearise<M, TEAM>(c);
-    stage_schur<M, TEAM>(c, false);
+    stage_schur<M, TEAM>(c, true);
     stage_precond<M, TEAM>(c);
+    copy_lam_to_lamp<M, TEAM>(c);
+    const int it = run_pcg<M, TEAM>(c);
+    stage_recover<M, TEAM>(c);
+    if (P.mode == MODE_INSPECT) { write_inspect<M, TEAM>(c, it); break; }
+    const float a = stage_linesearch<M, TEAM>(c);
+    if (c.tm.lane == 0) {
+      if (P.pcg_iters) P.pcg_iters[(long long)c.ocp * P.opt.sqp_iters + s] = it;
+      if (P.alpha_hist) P.alpha_hist[(long long)c.ocp * P.opt.sqp_iters + s] = a;
+    }
   }
-  // adjoint right-hand side: gamma~_spd = H G^-1 dl/dz (Eq. 7 with (-b, d) <- (dl/dz, 0))
+  if (P.mode == MODE_INSPECT) return;
+  stage_fwd_outputs<M, TEAM>(c);
+}
+
+// Backward right-hand side (Eq. 7 with (-b, d) <- (dl/dz, 0)): gamma~_spd = H G^-1 dl/dz,
+// and the adjoint PCG's initial guess (the previous adjoint multipliers or 0).
+template <class M, int TEAM>
+__device__ __noinline__ void stage_bwd_rhs(Ctx<M, TEAM>& c) {
+  constexpr int NX = M::NX, NU = M::NU, NZ = NX + NU;
+  const KParams& P = *c.P;
+  const int K = c.K, KP = c.KP;
   const float* g = P.dl_dz + c.o.z_off;
   const float* A = c.F(c.L.A);
   const float* Bm = c.F(c.L.Bm);
@@ -1292,14 +1310,14 @@ __device__ __noinline__ void run_backward(Ctx<M, TEAM>& c) {
   for (int k = c.tm.lane; k < K; k += TEAM) {
     double s[NX];
 #pragma unroll
-    for (int i = 0; i < NX; ++i) s[i] = (double)g[(long long)k * NZ + i] / (double)c.qproj(k, i);
+    for (int i = 0; i < NX; ++i) s[i] = (double)g[(long long)k * NZ + i] * c.qinv(k, i);
     if (k > 0) {
       const int t = k - 1;
       double vx[NX], vu[NU];
 #pragma unroll
-      for (int j = 0; j < NX; ++j) vx[j] = (double)g[(long long)t * NZ + j] / (double)c.qproj(t, j);
+      for (int j = 0; j < NX; ++j) vx[j] = (double)g[(long long)t * NZ + j] * c.qinv(t, j);
 #pragma unroll
-      for (int j = 0; j < NU; ++j) vu[j] = (double)g[(long long)t * NZ + NX + j] / (double)c.misc(MS_RP + j);
+      for (int j = 0; j < NU; ++j) vu[j] = (double)g[(long long)t * NZ + NX + j] * c.rinv(j);
 #pragma unroll
       for (int i = 0; i < NX; ++i) {
 #pragma unroll
@@ -1316,7 +1334,17 @@ __device__ __noinline__ void run_backward(Ctx<M, TEAM>& c) {
     }
   }
   c.tm.sync();
-  const int it = run_pcg<M, TEAM>(c);
+}
+
+// Backward finish: z~ = G^-1 (dl/dz - H^T lambda~) (Eq. 11 form), then
+// dl/dtheta = -(dF/dtheta)^T [z~; lambda~] contracted per knot (Eq. 3), dl/dx_s = lambda~_0.
+template <class M, int TEAM>
+__device__ __noinline__ void stage_bwd_finish(Ctx<M, TEAM>& c, int it) {
+  constexpr int NX = M::NX, NU = M::NU, NZ = NX + NU, NP = M::NP;
+  const KParams& P = *c.P;
+  const int T = c.T, K = c.K, KP = c.KP;
+  const float* g = P.dl_dz + c.o.z_off;
+  double* LP = c.Dp(c.L.d_lamp);
   // z~ = G^-1 (dl/dz - H^T lambda~)  (stored in xp, up)
   const double* WX = c.Dp(c.L.d_wx);
   const double* WU = c.Dp(c.L.d_wu);
@@ -1325,11 +1353,11 @@ __device__ __noinline__ void run_backward(Ctx<M, TEAM>& c) {
   for (int k = c.tm.lane; k < K; k += TEAM) {
 #pragma unroll
     for (int i = 0; i < NX; ++i)
-      XT[i * KP + k] = (float)(((double)g[(long long)k * NZ + i] - WX[i * KP + k]) / (double)c.qproj(k, i));
+      XT[i * KP + k] = (float)(((double)g[(long long)k * NZ + i] - WX[i * KP + k]) * c.qinv(k, i));
     if (k < T) {
 #pragma unroll
       for (int i = 0; i < NU; ++i)
-        UT[i * KP + k] = (float)(((double)g[(long long)k * NZ + NX + i] - WU[i * KP + k]) / (double)c.misc(MS_RP + i));
+        UT[i * KP + k] = (float)(((double)g[(long long)k * NZ + NX + i] - WU[i * KP + k]) * c.rinv(i));
     }
   }
   c.tm.sync();
@@ -1387,6 +1415,7 @@ __device__ __noinline__ void run_backward(Ctx<M, TEAM>& c) {
     }
   }
   c.tm.sum(red);
+  c.status = c.tm.bor(c.status);
   if (c.tm.lane == 0) {
 #pragma unroll
     for (int j = 0; j < NP; ++j) dth[j] = red[j];
@@ -1407,6 +1436,23 @@ __device__ __noinline__ void run_backward(Ctx<M, TEAM>& c) {
       if (P.res_lamt) P.res_lamt[lb + i] = v;
     }
   }
+}
+
+// Backward (Algorithm 3): adjoint PCG with the same S, z~, and the theta contraction.
+template <class M, int TEAM>
+__device__ __noinline__ void run_backward(Ctx<M, TEAM>& c) {
+  const KParams& P = *c.P;
+  stage_load<M, TEAM>(c, true);   // z (returned solution) and lambda (forward multipliers)
+  if (P.store_mode && P.store) {
+    store_blocks<M, TEAM>(c, true);
+  } else {
+    stage_linearise<M, TEAM>(c);
+    stage_schur<M, TEAM>(c, false);
+    stage_precond<M, TEAM>(c);
+  }
+  stage_bwd_rhs<M, TEAM>(c);
+  const int it = run_pcg<M, TEAM>(c);
+  stage_bwd_finish<M, TEAM>(c, it);
 }
 
 template <class M, int TEAM>

@@ -1,6 +1,11 @@
-// Fused SQP / backward kernels instantiated for the Attitude model.
+// Fused and plain kernels instantiated for the Attitude model, one team size per compilation
+// (the build compiles this file once per DMPC_TEAM in 32, 64, 128, 256).
 #include "launch_impl.cuh"
 
+#ifndef DMPC_TEAM
+#error "compile with -DDMPC_TEAM=<team size>"
+#endif
+
 namespace dmpc {
-int register_attitude(KernelEntry* out) { return register_teams<Attitude>(out, M_ATTITUDE); }
+int DMPC_REGISTER_NAME(attitude, DMPC_TEAM)(KernelEntry* out) { return register_team<Attitude, DMPC_TEAM>(out, M_ATTITUDE); }
 }  // namespace dmpc

@@ -1,6 +1,11 @@
-// Fused SQP / backward kernels instantiated for the CartPole model.
+// Fused and plain kernels instantiated for the CartPole model, one team size per compilation
+// (the build compiles this file once per DMPC_TEAM in 32, 64, 128, 256).
 #include "launch_impl.cuh"
 
+#ifndef DMPC_TEAM
+#error "compile with -DDMPC_TEAM=<team size>"
+#endif
+
 namespace dmpc {
-int register_cartpole(KernelEntry* out) { return register_teams<CartPole>(out, M_CARTPOLE); }
+int DMPC_REGISTER_NAME(cartpole, DMPC_TEAM)(KernelEntry* out) { return register_team<CartPole, DMPC_TEAM>(out, M_CARTPOLE); }
 }  // namespace dmpc

@@ -1,13 +1,18 @@
-// Fused SQP / backward kernels instantiated for LQ OCPs of the supported sizes.
+// Fused and plain kernels instantiated for LQ OCPs of the supported sizes, one team size per
+// compilation (the build compiles this file once per DMPC_TEAM in 32, 64, 128, 256).
 #include "launch_impl.cuh"
 
+#ifndef DMPC_TEAM
+#error "compile with -DDMPC_TEAM=<team size>"
+#endif
+
 namespace dmpc {
-int register_lq(KernelEntry* out) {
+int DMPC_REGISTER_NAME(lq, DMPC_TEAM)(KernelEntry* out) {
   int n = 0;
-  n += register_teams<LQ<2, 1>>(out + n, M_LQ);
-  n += register_teams<LQ<3, 2>>(out + n, M_LQ);
-  n += register_teams<LQ<4, 1>>(out + n, M_LQ);
-  n += register_teams<LQ<8, 4>>(out + n, M_LQ);
+  n += register_team<LQ<2, 1>, DMPC_TEAM>(out + n, M_LQ);
+  n += register_team<LQ<3, 2>, DMPC_TEAM>(out + n, M_LQ);
+  n += register_team<LQ<4, 1>, DMPC_TEAM>(out + n, M_LQ);
+  n += register_team<LQ<8, 4>, DMPC_TEAM>(out + n, M_LQ);
   return n;
 }
 }  // namespace dmpc

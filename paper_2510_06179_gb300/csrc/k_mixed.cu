@@ -1,16 +1,16 @@
-// Registry entries of the mixed-model kernels (instantiated in k_mixed_<team>.cu).
-#include "launch.h"
+// Fused and plain kernels for batches that mix the nonlinear models: each team dispatches on
+// the model of the OCP it takes from the work list.  One team size per compilation.
+#include "launch_impl.cuh"
+
+#ifndef DMPC_TEAM
+#error "compile with -DDMPC_TEAM=<team size>"
+#endif
 
 namespace dmpc {
-LaunchFn mixed_launcher_32();
-LaunchFn mixed_launcher_64();
-LaunchFn mixed_launcher_128();
-LaunchFn mixed_launcher_256();
-int register_mixed(KernelEntry* out) {
-  out[0] = {-1, 0, 0, 32, mixed_launcher_32()};
-  out[1] = {-1, 0, 0, 64, mixed_launcher_64()};
-  out[2] = {-1, 0, 0, 128, mixed_launcher_128()};
-  out[3] = {-1, 0, 0, 256, mixed_launcher_256()};
-  return 4;
+int DMPC_REGISTER_NAME(mixed, DMPC_TEAM)(KernelEntry* out) {
+  out[0] = {-1, 0, 0, DMPC_TEAM,
+            &launch_fused<DMPC_TEAM, Pendulum, CartPole, KinBicycle, SingleTrack, RigidBody12, Attitude>,
+            &launch_plain<DMPC_TEAM, Pendulum, CartPole, KinBicycle, SingleTrack, RigidBody12, Attitude>};
+  return 1;
 }
 }  // namespace dmpc

@@ -1,6 +1,11 @@
-// Fused SQP / backward kernels instantiated for the Pendulum model.
+// Fused and plain kernels instantiated for the Pendulum model, one team size per compilation
+// (the build compiles this file once per DMPC_TEAM in 32, 64, 128, 256).
 #include "launch_impl.cuh"
 
+#ifndef DMPC_TEAM
+#error "compile with -DDMPC_TEAM=<team size>"
+#endif
+
 namespace dmpc {
-int register_pendulum(KernelEntry* out) { return register_teams<Pendulum>(out, M_PENDULUM); }
+int DMPC_REGISTER_NAME(pendulum, DMPC_TEAM)(KernelEntry* out) { return register_team<Pendulum, DMPC_TEAM>(out, M_PENDULUM); }
 }  // namespace dmpc

@@ -1,6 +1,11 @@
-// Fused SQP / backward kernels instantiated for the RigidBody12 model.
+// Fused and plain kernels instantiated for the RigidBody12 model, one team size per compilation
+// (the build compiles this file once per DMPC_TEAM in 32, 64, 128, 256).
 #include "launch_impl.cuh"
 
+#ifndef DMPC_TEAM
+#error "compile with -DDMPC_TEAM=<team size>"
+#endif
+
 namespace dmpc {
-int register_rigid_body(KernelEntry* out) { return register_teams<RigidBody12>(out, M_RIGID_BODY12); }
+int DMPC_REGISTER_NAME(rigid_body, DMPC_TEAM)(KernelEntry* out) { return register_team<RigidBody12, DMPC_TEAM>(out, M_RIGID_BODY12); }
 }  // namespace dmpc

@@ -7,21 +7,39 @@ namespace dmpc {
 
 typedef cudaError_t (*LaunchFn)(const KParams& P, int grid, int threads, size_t smem, cudaStream_t s);
 
+struct PlainState;
+// plain one-launch-per-step form: one launch = one step for the batch (grid = batch, block = team)
+typedef cudaError_t (*PlainFn)(const KParams& P, PlainState* st, int step, int s_iter, int grid, int threads,
+                               cudaStream_t s);
+
 struct KernelEntry {
   int model;   // model id, or -1 for the mixed kernel (all nonlinear models)
   int nx, nu;
   int team;
   LaunchFn fn;
+  PlainFn plain;
 };
 
-// each translation unit appends its entries; returns the number written
-int register_lq(KernelEntry* out);
-int register_pendulum(KernelEntry* out);
-int register_cartpole(KernelEntry* out);
-int register_bicycle(KernelEntry* out);
-int register_single_track(KernelEntry* out);
-int register_rigid_body(KernelEntry* out);
-int register_attitude(KernelEntry* out);
-int register_mixed(KernelEntry* out);
+// Each kernel translation unit is compiled once per team size and appends its entries;
+// the functions return the number of entries written.
+#define DMPC_REGISTER_NAME2(model, team) register_##model##_##team
+#define DMPC_REGISTER_NAME(model, team) DMPC_REGISTER_NAME2(model, team)
+#define DMPC_DECLARE_TEAMS(model)                 \
+  int DMPC_REGISTER_NAME(model, 32)(KernelEntry*);  \
+  int DMPC_REGISTER_NAME(model, 64)(KernelEntry*);  \
+  int DMPC_REGISTER_NAME(model, 128)(KernelEntry*); \
+  int DMPC_REGISTER_NAME(model, 256)(KernelEntry*);
+DMPC_DECLARE_TEAMS(lq)
+DMPC_DECLARE_TEAMS(pendulum)
+DMPC_DECLARE_TEAMS(cartpole)
+DMPC_DECLARE_TEAMS(bicycle)
+DMPC_DECLARE_TEAMS(single_track)
+DMPC_DECLARE_TEAMS(rigid_body)
+DMPC_DECLARE_TEAMS(attitude)
+DMPC_DECLARE_TEAMS(mixed)
+
+// Fill `out` with every compiled kernel entry; returns the count (at most kMaxKernelEntries).
+constexpr int kMaxKernelEntries = 160;
+int collect_kernel_entries(KernelEntry* out);
 
 }  // namespace dmpc

@@ -1,6 +1,7 @@
 // Launch helper shared by the kernel translation units.
 #pragma once
 #include "fused.cuh"
+#include "plain.cuh"
 #include "launch.h"
 
 namespace dmpc {
@@ -18,13 +19,16 @@ cudaError_t launch_fused(const KParams& P, int grid, int threads, size_t smem, c
   return cudaGetLastError();
 }
 
-template <class M>
-int register_teams(KernelEntry* out, int model_id) {
-  out[0] = {model_id, M::NX, M::NU, 32, &launch_fused<32, M>};
-  out[1] = {model_id, M::NX, M::NU, 64, &launch_fused<64, M>};
-  out[2] = {model_id, M::NX, M::NU, 128, &launch_fused<128, M>};
-  out[3] = {model_id, M::NX, M::NU, 256, &launch_fused<256, M>};
-  return 4;
+template <int TEAM, class... Ms>
+cudaError_t launch_plain(const KParams& P, PlainState* st, int step, int s_iter, int grid, int threads, cudaStream_t s) {
+  plain_kernel<TEAM, Ms...><<<grid, threads, 0, s>>>(P, st, step, s_iter);
+  return cudaGetLastError();
+}
+
+template <class M, int TEAM>
+int register_team(KernelEntry* out, int model_id) {
+  out[0] = {model_id, M::NX, M::NU, TEAM, &launch_fused<TEAM, M>, &launch_plain<TEAM, M>};
+  return 1;
 }
 
 }  // namespace dmpc

@@ -82,8 +82,9 @@ class OCPBatch:
     def _alloc(self, n, dtype=torch.float32):
         return torch.empty(n, dtype=dtype, device=self.device)
 
-    def solve(self, x_s, theta, x_ref=None, z_init=None, lam_init=None, out=None, want_stats=True):
-        """Forward pass.  Returns dict(z, lam, status, pcg_iters, alpha) of flat tensors."""
+    def solve(self, x_s, theta, x_ref=None, z_init=None, lam_init=None, out=None, want_stats=True, plain=False):
+        """Forward pass.  Returns dict(z, lam, status, pcg_iters, alpha) of flat tensors.
+        plain=True runs the one-launch-per-step comparator (dmpc_solve_plain)."""
         d = self.device
         _dev_f32(x_s, self.n_xs, "x_s", d)
         _dev_f32(theta, self.n_th, "theta", d)
@@ -101,13 +102,15 @@ class OCPBatch:
             it = it if it is not None else self._alloc(self.B * self.sqp_iters, torch.int32)
             al = al if al is not None else self._alloc(self.B * self.sqp_iters)
         self._set_stream()
-        code = self.lib.dmpc_solve(self.h, _ptr(x_s), _ptr(theta), _ptr(x_ref), _ptr(z_init), _ptr(lam_init),
-                                   _ptr(z), _ptr(lam), _ptr(st), _ptr(it), _ptr(al))
+        fn = self.lib.dmpc_solve_plain if plain else self.lib.dmpc_solve
+        code = fn(self.h, _ptr(x_s), _ptr(theta), _ptr(x_ref), _ptr(z_init), _ptr(lam_init),
+                  _ptr(z), _ptr(lam), _ptr(st), _ptr(it), _ptr(al))
         _lib.check(code, self.h)
         return dict(z=z, lam=lam, status=st, pcg_iters=it, alpha=al)
 
-    def vjp(self, dl_dz, out=None, want_stats=True):
-        """Backward pass at the last solution.  Returns dict(dtheta, dxs, lamt, status, pcg_iters)."""
+    def vjp(self, dl_dz, out=None, want_stats=True, plain=False):
+        """Backward pass at the last solution.  Returns dict(dtheta, dxs, lamt, status, pcg_iters).
+        plain=True runs the one-launch-per-step comparator (dmpc_vjp_plain)."""
         _dev_f32(dl_dz, self.n_z, "dl_dz", self.device)
         o = out or {}
         dth = o.get("dtheta") if o.get("dtheta") is not None else self._alloc(self.n_th)
@@ -120,7 +123,8 @@ class OCPBatch:
             st = st if st is not None else self._alloc(self.B, torch.int32)
             it = it if it is not None else self._alloc(self.B, torch.int32)
         self._set_stream()
-        code = self.lib.dmpc_vjp(self.h, _ptr(dl_dz), _ptr(dth), _ptr(dxs), _ptr(lamt), _ptr(st), _ptr(it))
+        fn = self.lib.dmpc_vjp_plain if plain else self.lib.dmpc_vjp
+        code = fn(self.h, _ptr(dl_dz), _ptr(dth), _ptr(dxs), _ptr(lamt), _ptr(st), _ptr(it))
         _lib.check(code, self.h)
         return dict(dtheta=dth, dxs=dxs, lamt=lamt, status=st, pcg_iters=it)
 
