@@ -160,6 +160,28 @@ dmpc_err dmpc_qp_inspect(dmpc_handle* h, const float* x_s, const float* theta, c
                          const float* z, const float* lam, float* record);
 dmpc_err dmpc_inspect_offsets(const dmpc_handle* h, long long* rec_off /* batch+1 */);
 
+/* Allocation-free forward solve for callers that cannot allocate device memory when they
+ * solve: a controller in a hard real-time loop restricted to memory reserved at start-up, a
+ * plug-in inside a framework whose allocator owns the device, or a process at its memory limit.
+ * The paper has no counterpart; it is the same forward pass as dmpc_solve (same kernels) for a
+ * uniform batch (every OCP has shape *desc), without a handle.
+ *   - Allocates nothing: no cudaMalloc/cudaFree or allocating library call.  Its scratch (record
+ *     table, work list, and the per-team workspace when an OCP does not fit in shared memory)
+ *     is one fixed device array of DMPC_NOALLOC_SCRATCH_BYTES that every GPU loading the library
+ *     holds until process exit.  Requests whose scratch would exceed it return DMPC_E_BUDGET.
+ *   - The first call on each device looks up that array's device address (once per device, with
+ *     the device current); make the first call on a device before any stream capture.
+ *   - Every call shares the array and overwrites it; calls that overlap on the GPU (different
+ *     streams, or different host threads) race.  Serialise them on one stream.
+ *   - No warm start and no dmpc_vjp: z_init / lam_init (nullable) give the initial guess, else
+ *     the cold start.  Arguments are as in dmpc_solve; opt may be NULL (defaults);
+ *     cuda_stream is a cudaStream_t (NULL = default stream).  Asynchronous on that stream. */
+#define DMPC_NOALLOC_SCRATCH_BYTES (4u << 20)
+dmpc_err dmpc_solve_noalloc(const dmpc_ocp_desc* desc, int batch, const dmpc_options* opt, void* cuda_stream,
+                            const float* x_s, const float* theta, const float* x_ref, const float* z_init,
+                            const float* lam_init, float* z_out, float* lam_out, int* status_out,
+                            int* pcg_iters_out, float* alpha_out);
+
 /* Change the stream used by later calls. */
 dmpc_err dmpc_set_stream(dmpc_handle* h, void* cuda_stream);
 

@@ -35,6 +35,8 @@ SIGNATURES = {
     "dmpc_vjp_plain": (c_int, [P, P, P, P, P, P, P]),
     "dmpc_qp_inspect": (c_int, [P, P, P, P, P, P, P]),
     "dmpc_inspect_offsets": (c_int, [P, P]),
+    "dmpc_solve_noalloc": (c_int, [ctypes.POINTER(dmpc_ocp_desc), c_int, ctypes.POINTER(dmpc_options), P,
+                                   P, P, P, P, P, P, P, P, P, P]),
     "dmpc_set_stream": (c_int, [P, P]),
     "dmpc_set_tiling": (c_int, [P, c_int, c_int]),
     "dmpc_get_tiling": (c_int, [P, P, P, P, P]),
