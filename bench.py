@@ -56,8 +56,25 @@ def dist_env():
 
 
 def workload(rank):
+    """Each rank solves its own 256 OCPs (weak scaling, no data exchange between ranks)."""
     from paper_2510_06179_gb300 import workloads
     return workloads.cartpole_config(B=B, T=T, seed=1000 + rank, sqp_iters=SQP_ITERS, pcg_tol=PCG_TOL)
+
+
+def max_over_ranks(seconds, device=None):
+    """Timed-region length of the slowest rank (measurement only: one scalar all-reduce)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(seconds)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(world, steps, seconds):
+    """Whole-job OCP solve+grad per second: all ranks' OCPs over the slowest rank's time."""
+    return world * B * steps / seconds
 
 
 # ---------------------------------------------------------------------- CPU oracle
@@ -250,12 +267,8 @@ def main():
         dist.barrier()
     step_ms = [e[0].elapsed_time(e[2]) for e in ev]
     fwd_ms = [e[0].elapsed_time(e[1]) for e in ev]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        tt = torch.tensor([total_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_s = float(tt.item())
-    value = world * B * args.steps / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dev)
+    value = throughput(world, args.steps, total_s)
     pcg_f = int(out["pcg_iters"].sum().item())
     pcg_b = int(gout["pcg_iters"].sum().item())
     status = out["status"].cpu().numpy()
@@ -290,11 +303,7 @@ def main():
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
     h2d = (h_xs.numel() + h_th.numel() + h_xr.numel() + h_ut.numel()) * 4
     d2h = (h_gth.numel() + h_gxs.numel() + 1) * 4
 
@@ -333,7 +342,7 @@ def main():
         "config": {"workload": WORKLOAD, "batch_per_gpu": B, "T": T, "sqp_iters": SQP_ITERS,
                    "pcg_tol": PCG_TOL, "l2": "flushed between timed steps (256 MB write)",
                    "tiling": tiling, "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "e2e": {"value": round(world * B * args.steps / e2e_s, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": round(throughput(world, args.steps, e2e_s), 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": 2 * args.steps,
         "roofline": roof,

@@ -7,7 +7,7 @@ import ctypes
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libdmpc.so")
+LIB_PATH = os.environ.get("DMPC_LIB") or os.path.join(_PKG, "_build", "libdmpc.so")
 
 c_int, c_float, c_void_p, c_ll = ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_longlong
 P = c_void_p
@@ -34,6 +34,10 @@ SIGNATURES = {
     "dmpc_solve_plain": (c_int, [P, P, P, P, P, P, P, P, P, P, P]),
     "dmpc_vjp_plain": (c_int, [P, P, P, P, P, P, P]),
     "dmpc_qp_inspect": (c_int, [P, P, P, P, P, P, P]),
+    "dmpc_set_ocps": (c_int, [P, c_int, P, P, P]),
+    "dmpc_solve_subset": (c_int, [P, P, c_int, P, P, P, P, P, P, P, P]),
+    "dmpc_solve_subset_plain": (c_int, [P, P, c_int, P, P, P, P, P, P, P, P]),
+    "dmpc_device_bytes": (ctypes.c_longlong, [P]),
     "dmpc_inspect_offsets": (c_int, [P, P]),
     "dmpc_solve_noalloc": (c_int, [ctypes.POINTER(dmpc_ocp_desc), c_int, ctypes.POINTER(dmpc_options), P,
                                    P, P, P, P, P, P, P, P, P, P]),
