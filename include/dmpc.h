@@ -151,6 +151,28 @@ dmpc_err dmpc_solve_plain(dmpc_handle* h, const float* x_s, const float* theta, 
 dmpc_err dmpc_vjp_plain(dmpc_handle* h, const float* dl_dz, float* dl_dtheta, float* dl_dxs, float* lamt_out,
                         int* status_out, int* pcg_iters_out);
 
+/* Serving (continuous batching).  A handle's OCPs act as slots: the shapes given at creation
+ * are each slot's capacity, and a slot can later hold any OCP that fits it.
+ *   dmpc_set_ocps: re-describe slots index[0..n-1] (host arrays) with descs[i]; reset[i] != 0
+ *     (host, nullable) makes the slot's next solve start cold instead of from its resident
+ *     iterate.  Shapes must fit the slot (n, m, p, x_ref length and workspace) else
+ *     DMPC_E_BUDGET; a single-model handle keeps its model.  Ordered on the handle's stream.
+ *   dmpc_solve_subset: run opt.sqp_iters SQP iterations (Algorithm 2) on the slots listed in the
+ *     DEVICE array index[0..n-1], each continuing from its resident iterate (or cold when reset);
+ *     arrays are the handle-wide packed arrays of dmpc_layout (only listed slots are read or
+ *     written).  With sqp_iters = 1 every call advances each listed problem by one SQP
+ *     iteration, so requests can join between calls (continuous batching).
+ *   dmpc_solve_subset_plain: the same on the plain one-launch-per-step form.
+ *   dmpc_device_bytes: device memory owned by the handle (for budget-based admission). */
+dmpc_err dmpc_set_ocps(dmpc_handle* h, int n, const int* index, const dmpc_ocp_desc* descs, const int* reset);
+dmpc_err dmpc_solve_subset(dmpc_handle* h, const int* index, int n, const float* x_s, const float* theta,
+                           const float* x_ref, float* z_out, float* lam_out, int* status_out, int* pcg_iters_out,
+                           float* alpha_out);
+dmpc_err dmpc_solve_subset_plain(dmpc_handle* h, const int* index, int n, const float* x_s, const float* theta,
+                                 const float* x_ref, float* z_out, float* lam_out, int* status_out,
+                                 int* pcg_iters_out, float* alpha_out);
+long long dmpc_device_bytes(const dmpc_handle* h);
+
 /* Diagnostic: build and solve ONE QP at (z, lam) for every OCP (Eq. 4, 8-11, Algorithm 4)
  * and write a record per OCP at record + rec_off[b] (rec_off from dmpc_inspect_offsets):
  *   A_t (T nx nx), B_t (T nx nu), C_t (T nx), g (K nx: x_0 - x_s, f_0..f_{T-1}),

@@ -19,10 +19,10 @@
 using namespace dmpc;
 
 namespace dmpc {
-__global__ void plain_count_active(const PlainState* st, int n, int* out) {
+__global__ void plain_count_active(const PlainState* st, const int* order, int n, int* out) {
   __shared__ int part[256];
   int acc = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += st[i].active;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += st[order ? order[i] : i].active;
   part[threadIdx.x] = acc;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -111,6 +111,12 @@ struct dmpc_handle {
   LaunchFn fn = nullptr;
   PlainFn plain_fn = nullptr;
   // plain one-launch-per-step form (allocated on first use)
+  // serving: slot capacities (the shapes given at creation), cold-start flags, update staging
+  std::vector<OcpRec> cap;
+  unsigned char* d_cold = nullptr;
+  OcpRec* d_upd = nullptr;
+  int* d_upd_idx = nullptr;
+  size_t bytes = 0;
   float* plain_ws = nullptr;
   PlainState* plain_st = nullptr;
   int* plain_dcount = nullptr;
@@ -314,6 +320,16 @@ extern "C" dmpc_err dmpc_create_problem_batch(const dmpc_ocp_desc* descs, int ba
       return fail(nullptr, DMPC_E_OOM, "stored-Schur buffer allocation failed");
     }
   }
+  if (dmal((void**)&h->d_cold, batch) != cudaSuccess || dmal((void**)&h->d_upd, sizeof(OcpRec) * batch) != cudaSuccess ||
+      dmal((void**)&h->d_upd_idx, sizeof(int) * 2 * batch) != cudaSuccess) {
+    dmpc_destroy(h);
+    return fail(nullptr, DMPC_E_OOM, "device allocation failed");
+  }
+  cudaMemset(h->d_cold, 0, batch);
+  h->cap = h->recs;
+  h->bytes = sizeof(OcpRec) * batch * 2 + sizeof(int) * batch * 3 + sizeof(long long) * (batch + 1) + batch +
+             sizeof(float) * (h->tot_z + h->tot_xs + h->tot_th + h->tot_xref) + sizeof(double) * 2 * h->tot_lam +
+             (h->store ? sizeof(float) * h->tot_store : 0);
   ce = cudaMemcpy(h->d_recs, h->recs.data(), sizeof(OcpRec) * batch, cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(h->d_order, h->order.data(), sizeof(int) * batch, cudaMemcpyHostToDevice);
   if (ce == cudaSuccess)
@@ -497,7 +513,7 @@ static dmpc_err plain_prepare(dmpc_handle* h, KParams* P) {
 }
 
 static dmpc_err plain_pcg(dmpc_handle* h, const KParams& P) {
-  auto L = [&](int step) { return h->plain_fn(P, h->plain_st, step, 0, h->batch, h->team, h->stream); };
+  auto L = [&](int step) { return h->plain_fn(P, h->plain_st, step, 0, P.n_work, h->team, h->stream); };
   const int maxit = h->opt.pcg_max_iters;
   for (int base = 0; base < maxit; base += kPlainPoll) {
     for (int j = 0; j < kPlainPoll; ++j) {
@@ -505,7 +521,8 @@ static dmpc_err plain_pcg(dmpc_handle* h, const KParams& P) {
           L(PS_BETA) != cudaSuccess)
         return fail(h, DMPC_E_CUDA, "plain PCG launch failed");
     }
-    plain_count_active<<<1, 256, 0, h->stream>>>(h->plain_st, h->batch, h->plain_dcount);
+    plain_count_active<<<1, 256, 0, h->stream>>>(h->plain_st, P.order == h->d_order ? nullptr : P.order, P.n_work,
+                                                  h->plain_dcount);
     cudaMemcpyAsync(h->plain_hcount, h->plain_dcount, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "plain PCG poll");
@@ -595,6 +612,136 @@ extern "C" dmpc_err dmpc_vjp_plain(dmpc_handle* h, const float* dl_dz, float* dl
   return DMPC_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// Serving: re-describe slots within their capacity and solve a subset of them.
+namespace dmpc {
+__global__ void apply_slot_updates(OcpRec* recs, unsigned char* cold, const OcpRec* upd, const int* idx_reset,
+                                   int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int b = idx_reset[2 * i];
+    recs[b] = upd[i];
+    if (idx_reset[2 * i + 1]) cold[b] = 1;
+  }
+}
+}  // namespace dmpc
+
+extern "C" dmpc_err dmpc_set_ocps(dmpc_handle* h, int n, const int* index, const dmpc_ocp_desc* descs,
+                                  const int* reset) {
+  if (!h || n < 0 || (n > 0 && (!index || !descs))) return DMPC_E_ARG;
+  if (n == 0) return DMPC_OK;
+  if (n > h->batch) return fail(h, DMPC_E_ARG, "more updates than slots");
+  std::vector<OcpRec> upd(n);
+  std::vector<int> idx_reset(2 * n);
+  for (int i = 0; i < n; ++i) {
+    const int b = index[i];
+    if (b < 0 || b >= h->batch) return fail(h, DMPC_E_ARG, "slot index out of range");
+    const dmpc_ocp_desc& d = descs[i];
+    ModelInfo mi;
+    if (!model_info(d.model, d.nx, d.nu, &mi) || d.T < 1) return fail(h, DMPC_E_UNSUPPORTED, "bad slot shape");
+    if (h->uniform && (d.model != h->model0 || d.nx != h->nx0 || d.nu != h->nu0))
+      return fail(h, DMPC_E_UNSUPPORTED, "a single-model handle cannot take another model");
+    if (d.model != DMPC_MODEL_LQ && !(d.dt > 0.f)) return fail(h, DMPC_E_ARG, "dt must be positive");
+    const OcpRec& c = h->cap[b];
+    OcpRec r = c;
+    const int K = d.T + 1;
+    r.model = d.model; r.nx = d.nx; r.nu = d.nu; r.T = d.T; r.dt = d.dt;
+    r.n = K * d.nx + d.T * d.nu;
+    r.m = K * d.nx;
+    r.p = mi.p_shared + d.T * p_knot(d.model, d.nx, d.nu) + 2 * d.nx + d.nu;
+    if (r.n > c.n || r.m > c.m || r.p > c.p || d.nx > c.nx || (long long)K * d.nx > (long long)(c.T + 1) * c.nx ||
+        (long long)K * (5 * d.nx * d.nx + d.nx * d.nu) > (long long)(c.T + 1) * (5 * c.nx * c.nx + c.nx * c.nu) ||
+        make_layout(d.nx, d.nu, K, h->team).total_floats > h->max_ws_floats)
+      return fail(h, DMPC_E_BUDGET, "shape exceeds the slot's capacity");
+    h->recs[b] = r;
+    upd[i] = r;
+    idx_reset[2 * i] = b;
+    idx_reset[2 * i + 1] = reset ? reset[i] : 0;
+  }
+  // pageable sources: the copies are staged before these calls return
+  cudaError_t e = cudaMemcpyAsync(h->d_upd, upd.data(), sizeof(OcpRec) * n, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_upd_idx, idx_reset.data(), sizeof(int) * 2 * n, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "slot update upload");
+  apply_slot_updates<<<(n + 255) / 256, 256, 0, h->stream>>>(h->d_recs, h->d_cold, h->d_upd, h->d_upd_idx, n);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "slot update");
+  return DMPC_OK;
+}
+
+static dmpc_err subset_common(dmpc_handle* h, const int* index, int n, const float* x_s, const float* theta,
+                              const float* x_ref, float* z_out, KParams* P) {
+  if (!h) return DMPC_E_ARG;
+  if (n < 0 || n > h->batch) return fail(h, DMPC_E_ARG, "subset size out of range");
+  REQUIRE_DEV(index, "index");
+  REQUIRE_DEV(x_s, "x_s");
+  REQUIRE_DEV(theta, "theta");
+  REQUIRE_DEV(z_out, "z_out");
+  OPTIONAL_DEV(x_ref, "x_ref");
+  *P = base_params(h);
+  P->order = index;
+  P->n_work = n;
+  P->cold = h->d_cold;
+  P->mode = MODE_SOLVE;
+  P->x_s = x_s; P->theta = theta; P->x_ref = x_ref;
+  // every slot continues from its resident iterate unless it was reset
+  P->z_init = h->res_z;
+  P->lam_init_d = h->res_lam;
+  P->z_out = z_out;
+  P->res_z = h->res_z; P->res_lam = h->res_lam;
+  P->res_xs = h->res_xs; P->res_th = h->res_th; P->res_xref = h->res_xref;
+  return DMPC_OK;
+}
+
+extern "C" dmpc_err dmpc_solve_subset(dmpc_handle* h, const int* index, int n, const float* x_s, const float* theta,
+                                      const float* x_ref, float* z_out, float* lam_out, int* status_out,
+                                      int* pcg_iters_out, float* alpha_out) {
+  KParams P;
+  dmpc_err er = subset_common(h, index, n, x_s, theta, x_ref, z_out, &P);
+  if (er != DMPC_OK || n == 0) return er;
+  OPTIONAL_DEV(lam_out, "lam_out");
+  P.lam_out = lam_out; P.status = status_out; P.pcg_iters = pcg_iters_out; P.alpha_hist = alpha_out;
+  const int grid = std::max(1, std::min(h->grid, (n + h->tpb - 1) / h->tpb));
+  cudaError_t e = h->fn(P, grid, h->team * h->tpb, h->smem, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+  h->have_solution = true;
+  h->last_had_xref = x_ref != nullptr;
+  return DMPC_OK;
+}
+
+extern "C" dmpc_err dmpc_solve_subset_plain(dmpc_handle* h, const int* index, int n, const float* x_s,
+                                            const float* theta, const float* x_ref, float* z_out, float* lam_out,
+                                            int* status_out, int* pcg_iters_out, float* alpha_out) {
+  KParams P;
+  dmpc_err er = subset_common(h, index, n, x_s, theta, x_ref, z_out, &P);
+  if (er != DMPC_OK || n == 0) return er;
+  OPTIONAL_DEV(lam_out, "lam_out");
+  er = plain_prepare(h, &P);
+  if (er != DMPC_OK) return er;
+  P.lam_out = lam_out; P.status = status_out; P.pcg_iters = pcg_iters_out; P.alpha_hist = alpha_out;
+  auto L = [&](int step, int s) { return h->plain_fn(P, h->plain_st, step, s, n, h->team, h->stream); };
+  if (L(PS_LOAD, 0) != cudaSuccess) return fail(h, DMPC_E_CUDA, "plain launch failed");
+  for (int s = 0; s < h->opt.sqp_iters; ++s) {
+    if (L(PS_LIN, s) != cudaSuccess || L(PS_SCHUR, s) != cudaSuccess || L(PS_PREC, s) != cudaSuccess ||
+        L(PS_PCG_SETUP, s) != cudaSuccess)
+      return fail(h, DMPC_E_CUDA, "plain launch failed");
+    er = plain_pcg(h, P);
+    if (er != DMPC_OK) return er;
+    if (L(PS_PCG_FINISH, s) != cudaSuccess || L(PS_RECOVER, s) != cudaSuccess || L(PS_LS, s) != cudaSuccess)
+      return fail(h, DMPC_E_CUDA, "plain launch failed");
+  }
+  if (L(PS_FWD_OUT, 0) != cudaSuccess) return fail(h, DMPC_E_CUDA, "plain launch failed");
+  h->have_solution = true;
+  h->last_had_xref = x_ref != nullptr;
+  return DMPC_OK;
+}
+
+extern "C" long long dmpc_device_bytes(const dmpc_handle* h) {
+  if (!h) return -1;
+  long long b = (long long)h->bytes + (long long)h->gws_floats * (long long)sizeof(float);
+  if (h->plain_ws) b += (long long)h->plain_ws_floats * h->batch * (long long)sizeof(float) + (long long)sizeof(PlainState) * h->batch;
+  return b;
+}
+
 extern "C" dmpc_err dmpc_set_stream(dmpc_handle* h, void* s) {
   if (!h) return DMPC_E_ARG;
   h->stream = (cudaStream_t)s;
@@ -634,6 +781,9 @@ extern "C" void dmpc_destroy(dmpc_handle* h) {
   cudaFree(h->res_xref);
   cudaFree(h->store);
   cudaFree(h->gws);
+  cudaFree(h->d_cold);
+  cudaFree(h->d_upd);
+  cudaFree(h->d_upd_idx);
   cudaFree(h->plain_ws);
   cudaFree(h->plain_st);
   cudaFree(h->plain_dcount);

@@ -263,7 +263,9 @@ __device__ __noinline__ void stage_load(Ctx<M, TEAM>& c, bool use_z_init) {
   float* X = c.F(c.L.x);
   float* U = c.F(c.L.u);
   double* LAM = c.Dp(c.L.d_lam);
-  const float* zi = use_z_init ? P.z_init : nullptr;
+  // a slot re-assigned to a new problem starts cold (its resident iterate belongs to the old one)
+  const bool cold = P.cold != nullptr && P.cold[c.ocp] != 0 && P.mode == MODE_SOLVE;
+  const float* zi = (use_z_init && !cold) ? P.z_init : nullptr;
   for (int k = c.tm.lane; k < K; k += TEAM) {
     const long long zb = c.o.z_off + (long long)k * NZ;
 #pragma unroll
@@ -277,7 +279,8 @@ __device__ __noinline__ void stage_load(Ctx<M, TEAM>& c, bool use_z_init) {
     for (int i = 0; i < NX; ++i) {
       double v = 0.0;
       if (P.mode != MODE_VJP) {
-        if (P.lam_init_d) v = P.lam_init_d[lb + i];
+        if (cold) v = 0.0;
+        else if (P.lam_init_d) v = P.lam_init_d[lb + i];
         else if (P.lam_init_f) v = (double)P.lam_init_f[lb + i];
       } else {
         v = P.lam_init_d ? P.lam_init_d[lb + i] : (P.lam_init_f ? (double)P.lam_init_f[lb + i] : 0.0);
@@ -286,6 +289,7 @@ __device__ __noinline__ void stage_load(Ctx<M, TEAM>& c, bool use_z_init) {
     }
   }
   c.tm.sync();
+  if (cold && c.tm.lane == 0) P.cold[c.ocp] = 0;
   if (c.misc(MS_BAD) != 0.f) c.status |= ST_BAD_INPUT;
 }
 

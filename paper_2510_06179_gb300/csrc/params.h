@@ -32,6 +32,7 @@ struct KParams {
   const OcpRec* ocps;
   const int* order;          // work list (OCP indices), heaviest first
   int n_work;
+  unsigned char* cold;       // per-OCP flags (may be null): start this OCP cold, then clear the flag
   int mode;
   Options opt;
   // inputs

@@ -234,8 +234,8 @@ __device__ void plain_one(const KParams& P, PlainState* st, int ocp, int step, i
 template <int TEAM, class... Ms>
 __global__ void __launch_bounds__(256, 1) plain_kernel(const __grid_constant__ KParams P, PlainState* st, int step,
                                                         int s_iter) {
-  const int ocp = blockIdx.x;
-  if (ocp >= P.n_work) return;
+  if ((int)blockIdx.x >= P.n_work) return;
+  const int ocp = P.order ? P.order[blockIdx.x] : (int)blockIdx.x;
   const OcpRec& o = P.ocps[ocp];
   bool done = ((o.model == Ms::ID && o.nx == Ms::NX && o.nu == Ms::NU
                     ? (plain_one<Ms, TEAM>(P, st, ocp, step, s_iter), true)
@@ -244,6 +244,6 @@ __global__ void __launch_bounds__(256, 1) plain_kernel(const __grid_constant__ K
 }
 
 // Number of OCPs whose PCG is still iterating (the host polls it).
-__global__ void plain_count_active(const PlainState* st, int n, int* out);
+__global__ void plain_count_active(const PlainState* st, const int* order, int n, int* out);
 
 }  // namespace dmpc
