@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=256, help="OCPs in the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--suite", default=None, help="also run the comparison suite and write it to this JSON file")
+    ap.add_argument("--suite-only", action="store_true", help="run only the comparison suite")
     return ap.parse_args()
 
 
@@ -198,6 +200,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.suite_only:
+        return suite(args.suite or "suite.json")
     import torch
     import torch.distributed as dist
     if world > 1:
@@ -355,6 +359,116 @@ def main():
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+    if args.suite:
+        suite(args.suite)
+
+
+# ---------------------------------------------------------------------- comparison suite
+def _timed(fn, reps, warm=2):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps / 1e3, (time.perf_counter() - t0) / reps
+
+
+def _fused_vs_plain(batch, inputs, dl, reps, n_ocps):
+    """Seconds per forward+backward step: fused (one launch each) and plain (one launch per step)."""
+    fused = lambda: (batch.solve(*inputs, want_stats=False), batch.vjp(dl, want_stats=False))
+    plain = lambda: (batch.solve(*inputs, want_stats=False, plain=True), batch.vjp(dl, want_stats=False, plain=True))
+    tf, _ = _timed(fused, reps)
+    tp, tp_wall = _timed(plain, max(1, reps // 4), warm=1)
+    return {"fused_solves_per_s": n_ocps / tf, "plain_solves_per_s": n_ocps / max(tp, tp_wall),
+            "fused_ms": tf * 1e3, "plain_ms": max(tp, tp_wall) * 1e3, "speedup": max(tp, tp_wall) / tf}
+
+
+def suite(path):
+    """Fused vs plain on the other workloads; uneven batch with autotuning and a CUDA graph;
+    serving p50/p99 against arrival rate.  Writes a JSON file and prints it."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2510_06179_gb300 import workloads, autotune
+    from paper_2510_06179_gb300.solver import OCPBatch
+    dev = torch.device("cuda", 0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32).reshape(-1)).to(dev)
+    out = {"device": torch.cuda.get_device_name(dev)}
+
+    # cart-pole batch (the headline workload): fused vs plain
+    w = workload(0)
+    b = OCPBatch(("cartpole", 4, 1, T, 0.05), batch=B, device=dev, sqp_iters=SQP_ITERS, line_search=1,
+                 pcg_tol=PCG_TOL, warm_start=0)
+    inp = (t(w.x_s), t(w.theta), t(w.x_ref))
+    z = b.solve(*inp)["z"]
+    dl = torch.zeros_like(z)
+    dl.view(B, -1)[:, 4] = 1.0
+    out["cartpole_b256"] = _fused_vs_plain(b, inp, dl, 5, B)
+    b.close()
+
+    # uneven batch: 4096 OCPs of three models, T ~ U{16..128}, one persistent launch,
+    # autotuned tiling, CUDA-graph replay
+    items = workloads.uneven_mix(n_ocps=4096, seed=0, sqp_iters=SQP_ITERS, pcg_tol=PCG_TOL)
+    b = OCPBatch([(x.model, x.nx, x.nu, x.T, x.dt) for x in items], device=dev, sqp_iters=SQP_ITERS,
+                 line_search=1, pcg_tol=PCG_TOL, warm_start=0)
+    cat = lambda f: t(np.concatenate([getattr(x, f).ravel() for x in items]))
+    inp = (cat("x_s"), cat("theta"), cat("x_ref"))
+    z = b.solve(*inp)["z"]
+    dl = torch.zeros_like(z)
+    dl[::11] = 1.0
+    default_tiling = b.get_tiling()
+    tuned = autotune.tune(b, inp, dl_dz=dl, reps=2, use_cache=False)
+    g = autotune.GraphStep(b, *inp, dl_dz=dl)
+    tg, _ = _timed(g.replay, 5)
+    cmp_ = _fused_vs_plain(b, inp, dl, 3, len(items))
+    out["uneven_4096"] = dict(cmp_, graph_solves_per_s=len(items) / tg, graph_ms=tg * 1e3,
+                              default_tiling=default_tiling, tuned=dict(team_threads=tuned["team_threads"],
+                                                                        teams_per_block=tuned["teams_per_block"],
+                                                                        ms=tuned["ms"]),
+                              table=tuned.get("table"))
+    b.close()
+
+    # vehicle: 1024 single-track OCPs, T = 100, dt = 0.02, forward + backward
+    w = workloads.vehicle_config(B=1024, T=100, seed=0, sqp_iters=SQP_ITERS)
+    b = OCPBatch(("single_track", 6, 2, 100, 0.02), batch=1024, device=dev, sqp_iters=SQP_ITERS, line_search=1,
+                 pcg_tol=PCG_TOL, warm_start=0)
+    inp = (t(w.x_s), t(w.theta), t(w.x_ref))
+    z = b.solve(*inp)["z"]
+    dl = torch.zeros_like(z)
+    dl.view(1024, -1)[:, 6] = 1.0
+    out["vehicle_b1024"] = _fused_vs_plain(b, inp, dl, 3, 1024)
+    b.close()
+
+    # serving: Poisson arrivals, nx in {2, 4, 6, 12}, T log-uniform in [16, 256]
+    from paper_2510_06179_gb300.serving import ServingEngine, Request, latency_stats
+    serving = {}
+    for plain in (False, True):
+        eng = ServingEngine(workloads.SERVING_SHAPES, budget_bytes=64 << 30, sqp_iters=5, slots_per_class=512,
+                            plain=plain, pcg_tol=PCG_TOL)
+        rows = {}
+        for rate in (1000, 5000, 10000, 20000, 50000):
+            dur = min(1.0, 20000 / rate)
+            trace = workloads.serving_trace(rate, dur, seed=rate)
+            reqs = [Request(rid=i, **d) for i, d in enumerate(trace)]
+            t0 = time.perf_counter()
+            eng.run(reqs, max_seconds=30.0)
+            wall = time.perf_counter() - t0
+            st = latency_stats(reqs)
+            st.update(rate=rate, requests=len(reqs), throughput_per_s=st["completed"] / wall)
+            rows[str(rate)] = st
+        serving["plain" if plain else "fused"] = rows
+        eng.close()
+    out["serving"] = serving
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out), file=sys.stderr)
+    return out
 
 
 def reference_arm(args, rank, world):

@@ -193,7 +193,8 @@ static dmpc_err configure_tiling(dmpc_handle* h, int team, int tpb) {
   for (auto& d : h->descs) maxnx = std::max(maxnx, d.nx);
   if (team == 0) {
     // one knot per lane (register-resident PCG) when it fits, else a few knots per lane
-    if (maxnx <= 4 && maxK <= 256) team = maxK <= 32 ? 32 : (maxK <= 64 ? 64 : (maxK <= 128 ? 128 : 256));
+    // nx <= 4: one warp with one or two knots per lane up to K = 64, else one knot per lane
+    if (maxnx <= 4 && maxK <= 256) team = maxK <= 64 ? 32 : (maxK <= 128 ? 128 : 256);
     else team = maxK <= 48 ? 32 : (maxK <= 160 ? 64 : (maxK <= 320 ? 128 : 256));
   }
   int ws = 0;

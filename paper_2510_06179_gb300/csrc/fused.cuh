@@ -998,11 +998,204 @@ __device__ __noinline__ int stage_pcg_reg(Ctx<M, TEAM>& c) {
   return it;
 }
 
+// Block-tridiagonal row product for KPL contiguous knots per lane (knots l*KPL + j) of one
+// warp, blocks in registers: out_j = Md_j v_j + Mo_j v_{j-1} + Mo_{j+1}^T v_{j+1}.  The
+// transposed products t_j = Mo_j^T v_j travel to the previous knot; across lanes both move by
+// shuffles (lane 0 receives zeros, lane 31 receives zeros).
+template <int NX, int KPL>
+__device__ __forceinline__ void warp_btmv(const float (&Md)[KPL][NX * NX], const float (&Mo)[KPL][NX * NX],
+                                          const float (&v)[KPL][NX], float (&out)[KPL][NX], int ln) {
+  float t[KPL][NX];
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int b = 0; b < NX; ++b) {
+      float a = 0.f;
+#pragma unroll
+      for (int i = 0; i < NX; ++i) a = fmaf(Mo[j][i * NX + b], v[j][i], a);
+      t[j][b] = a;
+    }
+  float vm[NX], tn[NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    vm[i] = __shfl_up_sync(0xffffffffu, v[KPL - 1][i], 1);
+    tn[i] = __shfl_down_sync(0xffffffffu, t[0][i], 1);
+    if (ln == 0) vm[i] = 0.f;
+    if (ln == 31) tn[i] = 0.f;
+  }
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      float a = (j + 1 < KPL) ? t[j + 1 < KPL ? j + 1 : 0][i] : tn[i];
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        const float prev = (j > 0) ? v[j > 0 ? j - 1 : 0][q] : vm[q];
+        a = fmaf(Md[j][i * NX + q], v[j][q], fmaf(Mo[j][i * NX + q], prev, a));
+      }
+      out[j][i] = a;
+    }
+}
+
+template <int NV>
+__device__ __forceinline__ void warp_sum(float (&v)[NV]) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
+}
+
+// a4, single-warp variant (TEAM = 32, KPL contiguous knots per lane, K <= 32 KPL, nx <= 4):
+// the same algorithm as stage_pcg (Algorithm 4 in FP32 with FP64 reliable updates and the
+// FP64 rescue), with the S and Phi^-1 blocks of the lane's knots in registers for the whole
+// solve and every neighbour exchange and reduction done with warp shuffles: no shared memory
+// and no barrier inside the iteration.
+template <class M, int KPL>
+__device__ __noinline__ int stage_pcg_warp(Ctx<M, 32>& c) {
+  constexpr int NX = M::NX;
+  const KParams& P = *c.P;
+  const int K = c.K, KP = c.KP;
+  const int ln = c.tm.lane;
+  float* R = c.F(c.L.r);
+  double* LP = c.Dp(c.L.d_lamp);
+  const double* G = c.Dp(c.L.d_gam);
+  const float tol2 = P.opt.pcg_tol * P.opt.pcg_tol;
+  const float dl2 = P.opt.ru_delta * P.opt.ru_delta;
+  float Dk[KPL][NX * NX], Ok[KPL][NX * NX], Pdk[KPL][NX * NX], Pok[KPL][NX * NX];
+  bool live[KPL];
+#pragma unroll
+  for (int j = 0; j < KPL; ++j) {
+    const int k = ln * KPL + j;
+    live[j] = k < K;
+#pragma unroll
+    for (int e = 0; e < NX * NX; ++e) {
+      Dk[j][e] = live[j] ? c.F(c.L.D)[e * KP + k] : 0.f;
+      Ok[j][e] = (live[j] && k > 0) ? c.F(c.L.O)[e * KP + k] : 0.f;
+      Pdk[j][e] = live[j] ? c.F(c.L.Pd)[e * KP + k] : 0.f;
+      Pok[j][e] = (live[j] && k > 0) ? c.F(c.L.Po)[e * KP + k] : 0.f;
+    }
+  }
+  // eta_0 = gamma^T Phi^-1 gamma, from the FP32-rounded gamma
+  float r[KPL][NX], z[KPL][NX], p[KPL][NX], y[KPL][NX], dl[KPL][NX];
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) r[j][i] = live[j] ? (float)G[i * KP + ln * KPL + j] : 0.f;
+  warp_btmv<NX, KPL>(Pdk, Pok, r, z, ln);
+  float e0[1] = {0.f};
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) e0[0] = fmaf(r[j][i], z[j][i], e0[0]);
+  warp_sum(e0);
+  const float eta0 = e0[0];
+  // true residual of the initial guess, preconditioned residual, first direction
+  hp_residual<M, 32>(c, LP);
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { r[j][i] = live[j] ? R[i * KP + ln * KPL + j] : 0.f; dl[j][i] = 0.f; }
+  warp_btmv<NX, KPL>(Pdk, Pok, r, z, ln);
+  float e1[1] = {0.f};
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { p[j][i] = z[j][i]; e1[0] = fmaf(r[j][i], z[j][i], e1[0]); }
+  warp_sum(e1);
+  float eta = e1[0];
+  float eta_ref = eta, eta_true = eta;
+  int it = 0, stall = 0;
+  bool converged = !(eta > tol2 * eta0);
+  bool folded = true;
+  const int maxit = P.opt.pcg_max_iters;
+  while (!converged && it < maxit) {
+    warp_btmv<NX, KPL>(Dk, Ok, p, y, ln);          // y = S p
+    float v[1] = {0.f};
+#pragma unroll
+    for (int j = 0; j < KPL; ++j)
+#pragma unroll
+      for (int i = 0; i < NX; ++i) v[0] = fmaf(p[j][i], y[j][i], v[0]);
+    warp_sum(v);
+    if (!(v[0] > 0.f) || !isfinite(v[0])) break;
+    const float alpha = __fdividef(eta, v[0]);
+#pragma unroll
+    for (int j = 0; j < KPL; ++j)
+#pragma unroll
+      for (int i = 0; i < NX; ++i) { dl[j][i] = fmaf(alpha, p[j][i], dl[j][i]); r[j][i] = fmaf(-alpha, y[j][i], r[j][i]); }
+    folded = false;
+    warp_btmv<NX, KPL>(Pdk, Pok, r, z, ln);        // z = Phi^-1 r
+    float e2[1] = {0.f};
+#pragma unroll
+    for (int j = 0; j < KPL; ++j)
+#pragma unroll
+      for (int i = 0; i < NX; ++i) e2[0] = fmaf(r[j][i], z[j][i], e2[0]);
+    warp_sum(e2);
+    float eta_new = e2[0];
+    ++it;
+    if (eta_new < dl2 * eta_ref || !(eta_new > tol2 * eta0) || it >= maxit || !isfinite(eta_new)) {
+      // reliable update: fold the FP32 correction into the FP64 solution, true residual
+#pragma unroll
+      for (int j = 0; j < KPL; ++j)
+        if (live[j])
+#pragma unroll
+          for (int i = 0; i < NX; ++i) { LP[i * KP + ln * KPL + j] += (double)dl[j][i]; dl[j][i] = 0.f; }
+      folded = true;
+      hp_residual<M, 32>(c, LP);
+#pragma unroll
+      for (int j = 0; j < KPL; ++j)
+#pragma unroll
+        for (int i = 0; i < NX; ++i) r[j][i] = live[j] ? R[i * KP + ln * KPL + j] : 0.f;
+      warp_btmv<NX, KPL>(Pdk, Pok, r, z, ln);
+      float e3[1] = {0.f};
+#pragma unroll
+      for (int j = 0; j < KPL; ++j)
+#pragma unroll
+        for (int i = 0; i < NX; ++i) e3[0] = fmaf(r[j][i], z[j][i], e3[0]);
+      warp_sum(e3);
+      eta_new = e3[0];
+      eta_ref = eta_new;
+      if (!(eta_new > tol2 * eta0)) { converged = true; break; }
+      if (!isfinite(eta_new)) break;
+      if (eta_new > 0.25f * eta_true) {
+        if (++stall >= 2) break;
+      } else {
+        stall = 0;
+      }
+      eta_true = eta_new;
+      if (it >= maxit) break;
+    }
+    const float beta = __fdividef(eta_new, eta);
+    eta = eta_new;
+#pragma unroll
+    for (int j = 0; j < KPL; ++j)
+#pragma unroll
+      for (int i = 0; i < NX; ++i) p[j][i] = fmaf(beta, p[j][i], z[j][i]);
+  }
+  if (!folded) {
+#pragma unroll
+    for (int j = 0; j < KPL; ++j)
+      if (live[j])
+#pragma unroll
+        for (int i = 0; i < NX; ++i) LP[i * KP + ln * KPL + j] += (double)dl[j][i];
+    hp_residual<M, 32>(c, LP);
+  }
+  if (!converged) {
+    c.status |= ST_FP64_RESCUE;
+    it += stage_pcg64<M, 32>(c, (double)eta0, maxit);
+  }
+  return it;
+}
+
 // PCG entry: the register-resident inner loop when one knot per lane fits (nx <= 4).
 template <class M, int TEAM>
 __device__ __forceinline__ int run_pcg(Ctx<M, TEAM>& c) {
   if constexpr (M::NX <= 4) {
-    if (c.K <= TEAM) return stage_pcg_reg<M, TEAM>(c);
+    if constexpr (TEAM == 32) {
+      if (c.K <= 32) return stage_pcg_warp<M, 1>(c);
+      if (c.K <= 64) return stage_pcg_warp<M, 2>(c);
+    } else {
+      if (c.K <= TEAM) return stage_pcg_reg<M, TEAM>(c);
+    }
   }
   return stage_pcg<M, TEAM>(c);
 }

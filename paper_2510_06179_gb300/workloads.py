@@ -291,3 +291,35 @@ def uneven_mix(n_ocps=4096, T_lo=16, T_hi=128, seed=0, sqp_iters=10, pcg_tol=1e-
                              sqp_iters=sqp_iters, pcg_tol=pcg_tol)
         out.append(w)
     return out
+
+
+# ----------------------------------------------------------------------------------------
+# Serving workload: Poisson arrivals of single-OCP requests of mixed state dimension and horizon.
+SERVING_SHAPES = (("pendulum", 2, 1, 0.05), ("cartpole", 4, 1, 0.05), ("single_track", 6, 2, 0.02),
+                  ("rigid_body12", 12, 4, 0.02))
+_SINGLE = {"pendulum": pendulum_config, "cartpole": cartpole_config, "single_track": vehicle_config,
+           "rigid_body12": rigid_body_config}
+
+
+def serving_trace(rate, duration, seed=0, T_lo=16, T_hi=256, shapes=SERVING_SHAPES):
+    """Requests arriving as a Poisson process of `rate` per second over `duration` seconds; each
+    draws its model uniformly from `shapes` (nx 2, 4, 6, 12) and its horizon log-uniformly in
+    [T_lo, T_hi].  Returns a list of dicts (arrival, model, nx, nu, T, dt, x_s, theta, x_ref)."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.poisson(rate * duration))
+    arrivals = np.sort(rng.uniform(0.0, duration, size=n))
+    kinds = rng.integers(0, len(shapes), size=n)
+    Ts = np.exp(rng.uniform(np.log(T_lo), np.log(T_hi + 1), size=n)).astype(int).clip(T_lo, T_hi)
+    seeds = rng.integers(0, 1 << 31, size=n)
+    out = [None] * n
+    # draw all requests of one (model, horizon) together
+    groups = {}
+    for i in range(n):
+        groups.setdefault((int(kinds[i]), int(Ts[i])), []).append(i)
+    for (kind, T), idx in groups.items():
+        model, nx, nu, dt = shapes[kind]
+        w = _SINGLE[model](B=len(idx), T=T, seed=int(seeds[idx[0]]), dt=dt)
+        for j, i in enumerate(idx):
+            out[i] = dict(arrival=float(arrivals[i]), model=model, nx=nx, nu=nu, T=T, dt=dt,
+                          x_s=w.x_s[j], theta=w.theta[j], x_ref=w.x_ref[j])
+    return out

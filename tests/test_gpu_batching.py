@@ -1,0 +1,78 @@
+"""Batching reshapings: the plain one-launch-per-step form computes the same results as the
+fused kernel; the autotuner's tiling and CUDA-graph replay leave results unchanged; an uneven
+batch of mixed models and horizons runs in one launch."""
+import numpy as np
+import pytest
+
+from paper_2510_06179_gb300 import workloads
+from tests.gpu_helpers import make_batch, gpu_solve, gpu_vjp, dev, ensure_built
+from tests.oracle_helpers import rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def test_plain_form_matches_fused_form():
+    import torch
+    w = workloads.cartpole_config(B=16, T=40, seed=21, sqp_iters=3)
+    b = make_batch(w, warm_start=0)
+    out_f = b.solve(dev(w.x_s), dev(w.theta), dev(w.x_ref))
+    torch.cuda.synchronize()
+    zf = out_f["z"].view(w.B, -1).cpu().numpy().astype(np.float64)
+    gf = b.vjp(dev(w.dl_dz(zf)))
+    torch.cuda.synchronize()
+    dthf = gf["dtheta"].view(w.B, -1).cpu().numpy().astype(np.float64)
+    out_p = b.solve(dev(w.x_s), dev(w.theta), dev(w.x_ref), plain=True)
+    torch.cuda.synchronize()
+    zp = out_p["z"].view(w.B, -1).cpu().numpy().astype(np.float64)
+    gp = b.vjp(dev(w.dl_dz(zp)), plain=True)
+    torch.cuda.synchronize()
+    dthp = gp["dtheta"].view(w.B, -1).cpu().numpy().astype(np.float64)
+    assert np.array_equal(out_f["alpha"].cpu().numpy(), out_p["alpha"].cpu().numpy())
+    assert rel_err(zp, zf).max() <= 1e-5
+    assert rel_err(dthp, dthf).max() <= 1e-4
+    b.close()
+
+
+def _mixed_batch(n, seed, sqp=3):
+    from paper_2510_06179_gb300.solver import OCPBatch
+    ensure_built()
+    items = workloads.uneven_mix(n_ocps=n, T_lo=16, T_hi=128, seed=seed, sqp_iters=sqp)
+    descs = [(w.model, w.nx, w.nu, w.T, w.dt) for w in items]
+    b = OCPBatch(descs, device="cuda:0", sqp_iters=sqp, line_search=1, pcg_tol=1e-9, warm_start=0)
+    cat = lambda f: dev(np.concatenate([getattr(w, f).ravel() for w in items]))
+    return b, items, (cat("x_s"), cat("theta"), cat("x_ref"))
+
+
+def test_autotuned_tiling_keeps_results():
+    import torch
+    from paper_2510_06179_gb300 import autotune
+    b, items, inp = _mixed_batch(40, seed=4)
+    base = b.solve(*inp)["z"].clone()
+    torch.cuda.synchronize()
+    res = autotune.tune(b, inp, reps=1, use_cache=False, teams=(64, 128), tpbs=(1, 2))
+    assert res["team_threads"] in (64, 128) and len(res["table"]) >= 2
+    z = b.solve(*inp)["z"]
+    torch.cuda.synchronize()
+    zz, bb = z.cpu().numpy().astype(np.float64), base.cpu().numpy().astype(np.float64)
+    for i in range(len(items)):
+        sl = slice(int(b.z_off[i]), int(b.z_off[i + 1]))
+        assert rel_err(zz[sl], bb[sl]) <= 1e-5
+    b.close()
+
+
+def test_cuda_graph_replay_matches_direct_calls():
+    import torch
+    from paper_2510_06179_gb300.autotune import GraphStep
+    b, items, inp = _mixed_batch(24, seed=6)
+    dl = torch.zeros(b.n_z, device="cuda:0")
+    dl[::7] = 1.0
+    direct = b.solve(*inp)["z"].clone()
+    gdir = b.vjp(dl)["dtheta"].clone()
+    torch.cuda.synchronize()
+    g = GraphStep(b, *inp, dl_dz=dl)
+    for _ in range(2):
+        out, gout = g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out["z"], direct)
+    assert torch.equal(gout["dtheta"], gdir)
+    b.close()

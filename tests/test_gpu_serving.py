@@ -1,0 +1,88 @@
+"""Serving (continuous batching): requests of mixed state dimension and horizon arrive over
+time, join the running batch between SQP iterations, and each result equals the result of the
+same problem solved alone (same team size: bitwise; the gate is the solution tolerance), and
+matches the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_2510_06179_gb300 import workloads
+from tests.gpu_helpers import ensure_built, dev
+from tests.oracle_helpers import rel_err
+
+pytestmark = pytest.mark.gpu
+
+SQP = 3
+
+
+def _serve(trace, plain=False, slots=6):
+    import torch
+    ensure_built()
+    from paper_2510_06179_gb300.serving import ServingEngine, Request
+    eng = ServingEngine(workloads.SERVING_SHAPES, budget_bytes=16 << 30, sqp_iters=SQP, slots_per_class=slots,
+                        plain=plain, pcg_tol=1e-9)
+    reqs = [Request(rid=i, **d) for i, d in enumerate(trace)]
+    eng.run(reqs, keep_solutions=True, max_seconds=120)
+    torch.cuda.synchronize()
+    return eng, reqs
+
+
+def _alone(r, team):
+    import torch
+    from paper_2510_06179_gb300.solver import OCPBatch
+    b = OCPBatch((r.model, r.nx, r.nu, r.T, r.dt), batch=1, device="cuda:0", sqp_iters=SQP, line_search=1,
+                 warm_start=0, pcg_tol=1e-9)
+    b.set_tiling(team, 1)
+    out = b.solve(dev(r.x_s), dev(r.theta), dev(r.x_ref))
+    torch.cuda.synchronize()
+    z = out["z"].cpu().numpy().astype(np.float64)
+    b.close()
+    return z
+
+
+def test_serving_result_same_alone_and_in_the_mix():
+    trace = workloads.serving_trace(rate=3000, duration=0.03, seed=5, T_lo=16, T_hi=100)
+    eng, reqs = _serve(trace)
+    assert all(r.done is not None for r in reqs)
+    assert all(r.done >= r.arrival for r in reqs)
+    rng = np.random.default_rng(0)
+    sample = rng.choice(len(reqs), size=min(12, len(reqs)), replace=False)
+    worst, bitwise = 0.0, 0
+    for i in sample:
+        r = reqs[i]
+        team = eng.class_of(r).batch.get_tiling()["team_threads"]
+        z_alone = _alone(r, team)
+        e = rel_err(r.z.astype(np.float64), z_alone)
+        worst = max(worst, e)
+        bitwise += int(np.array_equal(r.z.astype(np.float64), z_alone))
+    print(f"serving: {len(reqs)} requests, alone-vs-mix max rel diff {worst:.2e}, bitwise {bitwise}/{len(sample)}")
+    assert worst <= 1e-5
+    eng.close()
+
+
+def test_serving_results_match_the_oracle():
+    from oracle.models import make_model
+    from oracle.ocp import OCPBatch as OB
+    from oracle.sqp import sqp
+    trace = workloads.serving_trace(rate=2000, duration=0.02, seed=9, T_lo=16, T_hi=60)
+    eng, reqs = _serve(trace)
+    n_agree = n_checked = 0
+    for r in reqs[:10]:
+        ocp = OB(make_model(r.model, r.nx, r.nu, r.dt), r.T, r.x_s[None].astype(float), r.theta[None].astype(float),
+                 r.x_ref[None].astype(float))
+        ref = sqp(ocp, SQP, line_search_on=True)
+        e = rel_err(r.z.astype(np.float64), ref["z"][0])
+        n_checked += 1
+        n_agree += int(e <= 1e-4)
+    print(f"serving vs oracle: {n_agree}/{n_checked} within 1e-4")
+    assert n_agree >= 0.7 * n_checked
+    eng.close()
+
+
+def test_plain_form_serving_gives_the_same_results():
+    trace = workloads.serving_trace(rate=2000, duration=0.01, seed=11, T_lo=16, T_hi=60)
+    e1, r1 = _serve(trace)
+    e2, r2 = _serve(trace, plain=True)
+    worst = max(rel_err(a.z.astype(np.float64), b.z.astype(np.float64)) for a, b in zip(r1, r2))
+    print(f"plain vs fused serving: max rel diff {worst:.2e}")
+    assert worst <= 1e-5
+    e1.close(); e2.close()
