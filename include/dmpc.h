@@ -101,6 +101,10 @@ typedef struct {
   int store_schur;     /* 1: solve keeps the blocks at the returned z for vjp; 0: vjp recomputes; default 0 */
   int team_threads;    /* threads per OCP: 32, 64, 128 or 256; 0 = chosen from the horizon */
   int teams_per_block; /* OCPs per thread block; 0 = chosen from batch size and shared memory */
+  int pcg_precision;   /* 0: FP32 PCG iteration with FP64 reliable updates and a double-float rescue
+                          when it stagnates; 1: double-float PCG iteration throughout (about 48-bit
+                          arithmetic from FP32 instructions; single-warp teams with nx <= 4, the
+                          others behave as 0); default 0 */
 } dmpc_options;
 
 /* Fill *opt with the defaults above. */

@@ -151,6 +151,7 @@ extern "C" void dmpc_default_options(dmpc_options* o) {
   o->store_schur = 0;
   o->team_threads = 0;
   o->teams_per_block = 0;
+  o->pcg_precision = 0;
 }
 
 static Options to_kernel_options(const dmpc_options& o) {
@@ -165,6 +166,7 @@ static Options to_kernel_options(const dmpc_options& o) {
   k.pcg_tol = o.pcg_tol;
   k.pcg_max_iters = o.pcg_max_iters;
   k.ru_delta = o.ru_delta;
+  k.pcg_precision = o.pcg_precision;
   return k;
 }
 
@@ -182,6 +184,7 @@ static dmpc_err validate_options(dmpc_handle* h, const dmpc_options& o) {
       o.team_threads != 256)
     return fail(h, DMPC_E_ARG, "team_threads must be 0, 32, 64, 128 or 256");
   if (o.teams_per_block < 0) return fail(h, DMPC_E_ARG, "teams_per_block must be >= 0");
+  if (o.pcg_precision != 0 && o.pcg_precision != 1) return fail(h, DMPC_E_ARG, "pcg_precision must be 0 or 1");
   return DMPC_OK;
 }
 

@@ -20,6 +20,7 @@
 // u_k, lambda_k, Schur block row k, and the linearisation of dynamics step t = k - 1.
 #pragma once
 #include "device_util.cuh"
+#include "dfloat.cuh"
 #include "models.cuh"
 #include "params.h"
 
@@ -1045,6 +1046,229 @@ __device__ __forceinline__ void warp_sum(float (&v)[NV]) {
     for (int j = 0; j < NV; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
 }
 
+// Double-float PCG for the single-warp path (Algorithm 4 in about 48-bit arithmetic built from
+// FP32 instructions): the operator S = H G^-1 H^T is applied from the FP32 factors A_t, B_t and
+// the reciprocal weights (the same operator as the FP64 true residual), the preconditioner from
+// its FP32 blocks with the diagonal blocks symmetrised (so it is exactly symmetric), and the
+// vectors and the scalars alpha, beta, eta are double-float.  All state in registers,
+// neighbour exchanges by shuffles.  Used as the rescue of a stagnated FP32 iteration, or for
+// the whole solve when the options ask for it.
+
+// out = M v for a block-tridiagonal symmetric M (diagonal blocks Md, sub-diagonal blocks Mo),
+// v and out double-float; same data movement as warp_btmv.
+template <int NX, int KPL>
+__device__ __forceinline__ void warp_btmv_df(const float (&Md)[KPL][NX * NX], const float (&Mo)[KPL][NX * NX],
+                                             const dfl (&v)[KPL][NX], dfl (&out)[KPL][NX], int ln) {
+  dfl t[KPL][NX];
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int b = 0; b < NX; ++b) {
+      dfl a = df_make(0.f);
+#pragma unroll
+      for (int i = 0; i < NX; ++i) a = df_fmaf(a, Mo[j][i * NX + b], v[j][i]);
+      t[j][b] = a;
+    }
+  dfl vm[NX], tn[NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    vm[i].hi = __shfl_up_sync(0xffffffffu, v[KPL - 1][i].hi, 1);
+    vm[i].lo = __shfl_up_sync(0xffffffffu, v[KPL - 1][i].lo, 1);
+    tn[i].hi = __shfl_down_sync(0xffffffffu, t[0][i].hi, 1);
+    tn[i].lo = __shfl_down_sync(0xffffffffu, t[0][i].lo, 1);
+    if (ln == 0) vm[i] = df_make(0.f);
+    if (ln == 31) tn[i] = df_make(0.f);
+  }
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      dfl a = (j + 1 < KPL) ? t[j + 1 < KPL ? j + 1 : 0][i] : tn[i];
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        a = df_fmaf(a, Mo[j][i * NX + q], (j > 0) ? v[j > 0 ? j - 1 : 0][q] : vm[q]);
+        a = df_fmaf(a, Md[j][i * NX + q], v[j][q]);
+      }
+      out[j][i] = a;
+    }
+}
+
+template <class M, int KPL>
+__device__ __forceinline__ void warp_S_df(const float (&Ak)[KPL][M::NX * M::NX], const float (&Bk)[KPL][M::NX * M::NU],
+                                          const dfl (&qi)[KPL][M::NX], const dfl (&ri)[M::NU], const bool (&has_u)[KPL],
+                                          const dfl (&v)[KPL][M::NX], dfl (&out)[KPL][M::NX], int ln) {
+  constexpr int NX = M::NX, NU = M::NU;
+  // pass 1: w = H^T v.  Knot k+1 owns A_k (slot k+1) and sends A_k^T v_{k+1}, B_k^T v_{k+1}.
+  dfl t[KPL][NX], ub[KPL][NU];
+#pragma unroll
+  for (int j = 0; j < KPL; ++j) {
+#pragma unroll
+    for (int b = 0; b < NX; ++b) {
+      dfl a = df_make(0.f);
+#pragma unroll
+      for (int i = 0; i < NX; ++i) a = df_fmaf(a, Ak[j][i * NX + b], v[j][i]);
+      t[j][b] = a;
+    }
+#pragma unroll
+    for (int b = 0; b < NU; ++b) {
+      dfl a = df_make(0.f);
+#pragma unroll
+      for (int i = 0; i < NX; ++i) a = df_fmaf(a, Bk[j][i * NU + b], v[j][i]);
+      ub[j][b] = a;
+    }
+  }
+  dfl tn[NX], ubn[NU];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    tn[i].hi = __shfl_down_sync(0xffffffffu, t[0][i].hi, 1);
+    tn[i].lo = __shfl_down_sync(0xffffffffu, t[0][i].lo, 1);
+    if (ln == 31) tn[i] = df_make(0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < NU; ++i) {
+    ubn[i].hi = __shfl_down_sync(0xffffffffu, ub[0][i].hi, 1);
+    ubn[i].lo = __shfl_down_sync(0xffffffffu, ub[0][i].lo, 1);
+    if (ln == 31) ubn[i] = df_make(0.f);
+  }
+  // pass 2: G^-1 w, then H (G^-1 w); knot k needs the scaled w of knot k-1
+  dfl vx[KPL][NX], vu[KPL][NU];
+#pragma unroll
+  for (int j = 0; j < KPL; ++j) {
+#pragma unroll
+    for (int i = 0; i < NX; ++i) vx[j][i] = df_mul(df_add(v[j][i], (j + 1 < KPL) ? t[j + 1 < KPL ? j + 1 : 0][i] : tn[i]), qi[j][i]);
+#pragma unroll
+    for (int i = 0; i < NU; ++i)
+      vu[j][i] = has_u[j] ? df_mul((j + 1 < KPL) ? ub[j + 1 < KPL ? j + 1 : 0][i] : ubn[i], ri[i]) : df_make(0.f);
+  }
+  dfl vxm[NX], vum[NU];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    vxm[i].hi = __shfl_up_sync(0xffffffffu, vx[KPL - 1][i].hi, 1);
+    vxm[i].lo = __shfl_up_sync(0xffffffffu, vx[KPL - 1][i].lo, 1);
+    if (ln == 0) vxm[i] = df_make(0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < NU; ++i) {
+    vum[i].hi = __shfl_up_sync(0xffffffffu, vu[KPL - 1][i].hi, 1);
+    vum[i].lo = __shfl_up_sync(0xffffffffu, vu[KPL - 1][i].lo, 1);
+    if (ln == 0) vum[i] = df_make(0.f);
+  }
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      dfl a = vx[j][i];
+#pragma unroll
+      for (int q = 0; q < NX; ++q) a = df_fmaf(a, Ak[j][i * NX + q], (j > 0) ? vx[j > 0 ? j - 1 : 0][q] : vxm[q]);
+#pragma unroll
+      for (int q = 0; q < NU; ++q) a = df_fmaf(a, Bk[j][i * NU + q], (j > 0) ? vu[j > 0 ? j - 1 : 0][q] : vum[q]);
+      out[j][i] = a;
+    }
+}
+
+template <class M, int KPL>
+__device__ __noinline__ int stage_pcg_warp_df(Ctx<M, 32>& c, float eta0f, int maxit) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const KParams& P = *c.P;
+  const int K = c.K, KP = c.KP, T = c.T;
+  const int ln = c.tm.lane;
+  double* LP = c.Dp(c.L.d_lamp);
+  const double* G = c.Dp(c.L.d_gam);
+  float Pdk[KPL][NX * NX], Pok[KPL][NX * NX], Ak[KPL][NX * NX], Bk[KPL][NX * NU];
+  dfl qi[KPL][NX], ri[NU];
+  bool live[KPL], has_u[KPL];
+#pragma unroll
+  for (int j = 0; j < KPL; ++j) {
+    const int k = ln * KPL + j;
+    live[j] = k < K;
+    has_u[j] = k < T;
+#pragma unroll
+    for (int a = 0; a < NX; ++a)
+#pragma unroll
+      for (int b = 0; b < NX; ++b) {
+        // symmetrised diagonal block: exactly symmetric operator
+        const float pab = live[j] ? c.F(c.L.Pd)[(a * NX + b) * KP + k] : 0.f;
+        const float pba = live[j] ? c.F(c.L.Pd)[(b * NX + a) * KP + k] : 0.f;
+        Pdk[j][a * NX + b] = 0.5f * (pab + pba);
+      }
+#pragma unroll
+    for (int e = 0; e < NX * NX; ++e) {
+      Pok[j][e] = (live[j] && k > 0) ? c.F(c.L.Po)[e * KP + k] : 0.f;
+      Ak[j][e] = (live[j] && k > 0) ? c.F(c.L.A)[e * KP + k] : 0.f;
+    }
+#pragma unroll
+    for (int e = 0; e < NX * NU; ++e) Bk[j][e] = (live[j] && k > 0) ? c.F(c.L.Bm)[e * KP + k] : 0.f;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) qi[j][i] = live[j] ? df_from(c.qinv(k, i)) : df_make(0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < NU; ++i) ri[i] = df_from(c.rinv(i));
+  // stop when eta <= tol^2 eta_0, compared in double-float
+  const dfl thr = df_mulf(df_make(eta0f), P.opt.pcg_tol * P.opt.pcg_tol);
+  dfl x[KPL][NX], r[KPL][NX], p[KPL][NX], y[KPL][NX], z[KPL][NX];
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) x[j][i] = live[j] ? df_from(LP[i * KP + ln * KPL + j]) : df_make(0.f);
+  // r = gamma - S x, z = Phi^-1 r, p = z, eta = r^T z
+  warp_S_df<M, KPL>(Ak, Bk, qi, ri, has_u, x, y, ln);
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) r[j][i] = live[j] ? df_sub(df_from(G[i * KP + ln * KPL + j]), y[j][i]) : df_make(0.f);
+  warp_btmv_df<NX, KPL>(Pdk, Pok, r, z, ln);
+  dfl eta = df_make(0.f);
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { p[j][i] = z[j][i]; eta = df_add(eta, df_mul(r[j][i], z[j][i])); }
+  eta = df_warp_sum(eta);
+  int it = 0;
+  bool converged = !(eta.hi > thr.hi);
+  while (!converged && it < maxit) {
+    warp_S_df<M, KPL>(Ak, Bk, qi, ri, has_u, p, y, ln);
+    dfl v = df_make(0.f);
+#pragma unroll
+    for (int j = 0; j < KPL; ++j)
+#pragma unroll
+      for (int i = 0; i < NX; ++i) v = df_add(v, df_mul(p[j][i], y[j][i]));
+    v = df_warp_sum(v);
+    if (!(v.hi > 0.f) || !isfinite(v.hi)) { c.status |= ST_PCG_BREAKDOWN; break; }
+    const dfl alpha = df_div(eta, v);
+#pragma unroll
+    for (int j = 0; j < KPL; ++j)
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        x[j][i] = df_add(x[j][i], df_mul(alpha, p[j][i]));
+        r[j][i] = df_sub(r[j][i], df_mul(alpha, y[j][i]));
+      }
+    warp_btmv_df<NX, KPL>(Pdk, Pok, r, z, ln);
+    dfl eta_new = df_make(0.f);
+#pragma unroll
+    for (int j = 0; j < KPL; ++j)
+#pragma unroll
+      for (int i = 0; i < NX; ++i) eta_new = df_add(eta_new, df_mul(r[j][i], z[j][i]));
+    eta_new = df_warp_sum(eta_new);
+    ++it;
+    if (!(eta_new.hi > thr.hi)) { converged = true; break; }
+    if (!isfinite(eta_new.hi)) break;
+    const dfl beta = df_div(eta_new, eta);
+    eta = eta_new;
+#pragma unroll
+    for (int j = 0; j < KPL; ++j)
+#pragma unroll
+      for (int i = 0; i < NX; ++i) p[j][i] = df_add(z[j][i], df_mul(beta, p[j][i]));
+  }
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+    if (live[j])
+#pragma unroll
+      for (int i = 0; i < NX; ++i) LP[i * KP + ln * KPL + j] = df_to(x[j][i]);
+  hp_residual<M, 32>(c, LP);  // leaves w = H^T lambda for the recovery
+  if (!converged) c.status |= ST_PCG_MAXITER;
+  return it;
+}
+
 // a4, single-warp variant (TEAM = 32, KPL contiguous knots per lane, K <= 32 KPL, nx <= 4):
 // the same algorithm as stage_pcg (Algorithm 4 in FP32 with FP64 reliable updates and the
 // FP64 rescue), with the S and Phi^-1 blocks of the lane's knots in registers for the whole
@@ -1089,6 +1313,7 @@ __device__ __noinline__ int stage_pcg_warp(Ctx<M, 32>& c) {
     for (int i = 0; i < NX; ++i) e0[0] = fmaf(r[j][i], z[j][i], e0[0]);
   warp_sum(e0);
   const float eta0 = e0[0];
+  if (P.opt.pcg_precision == 1) return stage_pcg_warp_df<M, KPL>(c, eta0, P.opt.pcg_max_iters);
   // true residual of the initial guess, preconditioned residual, first direction
   hp_residual<M, 32>(c, LP);
 #pragma unroll
@@ -1181,7 +1406,7 @@ __device__ __noinline__ int stage_pcg_warp(Ctx<M, 32>& c) {
   }
   if (!converged) {
     c.status |= ST_FP64_RESCUE;
-    it += stage_pcg64<M, 32>(c, (double)eta0, maxit);
+    it += stage_pcg_warp_df<M, KPL>(c, eta0, maxit);
   }
   return it;
 }

@@ -24,6 +24,7 @@ struct Options {
   float pcg_tol;        // relative residual tolerance: sqrt(eta / eta_0) <= pcg_tol
   int pcg_max_iters;
   float ru_delta;       // reliable-update trigger: eta drops by ru_delta^2
+  int pcg_precision;    // 0: FP32 iteration + FP64 reliable updates; 1: double-float throughout
 };
 
 enum KernelMode : int { MODE_SOLVE = 0, MODE_INSPECT = 1, MODE_VJP = 2 };

@@ -115,6 +115,16 @@ def test_cartpole_forward_parity():
     b.close()
 
 
+def test_cartpole_double_float_pcg_parity():
+    """pcg_precision = 1: the whole PCG solve in double-float arithmetic (single-warp teams)
+    meets the same solution and gradient gates, and no OCP needs the rescue."""
+    w = workloads.cartpole_config(B=32, T=50, seed=3)
+    b, g, ref = _nonlinear_forward(w, pcg_precision=1, team_threads=32)
+    assert not (g["status"] & 64).any()
+    _grad_check(w, b, g)
+    b.close()
+
+
 @pytest.mark.parametrize("maker", [workloads.pendulum_config, workloads.bicycle_config])
 def test_other_small_models_forward_parity(maker):
     w = maker(B=32, T=40, seed=1, sqp_iters=6)
