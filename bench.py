@@ -539,8 +539,8 @@ def suite(path):
 
         tf_dev, tf_wall = _timed(fwd, 5, warm=1)
         tb_dev, tb_wall = _timed(fwd_bwd, 5, warm=1)
-        nx, nu, T, H, B_ = workloads.RL_PROBLEMS[pid]
-        rl[f"P{pid}"] = dict(nx=nx, nu=nu, T=T, H=H, B=B_, fwd_s=max(tf_dev, tf_wall), fwd_bwd_s=max(tb_dev, tb_wall))
+        shape = dict(zip(("nx", "nu", "T", "H", "B"), workloads.RL_PROBLEMS[pid]))
+        rl[f"P{pid}"] = dict(shape, fwd_s=max(tf_dev, tf_wall), fwd_bwd_s=max(tb_dev, tb_wall))
         batch.close()
     out["rl_closed_loop"] = rl
 

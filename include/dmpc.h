@@ -65,7 +65,9 @@ typedef enum {
 #define DMPC_S_PCG_BREAKDOWN 16  /* p^T S p <= 0 in PCG (S not positive definite numerically) */
 #define DMPC_S_CHOL_FAIL 32      /* a diagonal Schur block failed Cholesky (diagonal fallback used) */
 #define DMPC_S_FP64_RESCUE 64    /* informational: a PCG solve whose FP32 iteration stagnated or broke
-                                    down was finished with the operator applied in FP64 */
+                                    down was finished in extended precision (FP64 or double-float) */
+#define DMPC_S_HESS_INDEF 128    /* exact-Hessian vjp: a per-knot block of the Lagrangian Hessian was not
+                                    positive definite; its Gauss-Newton block was used instead */
 
 typedef enum {
   DMPC_MODEL_LQ = 0,
@@ -105,6 +107,10 @@ typedef struct {
                           when it stagnates; 1: double-float PCG iteration throughout (about 48-bit
                           arithmetic from FP32 instructions; single-warp teams with nx <= 4, the
                           others behave as 0); default 0 */
+  int exact_hessian;   /* 1: dmpc_vjp uses the exact Hessian of the Lagrangian in the KKT matrix (the
+                          dynamics curvature weighted by the forward multipliers, Sec. 3.4), so the
+                          gradient is exact for nonlinear dynamics; 0: Gauss-Newton (the paper's
+                          default); enlarges the workspace by (nx+nu)^2 doubles per knot; default 0 */
 } dmpc_options;
 
 /* Fill *opt with the defaults above. */
@@ -207,6 +213,17 @@ dmpc_err dmpc_solve_noalloc(const dmpc_ocp_desc* desc, int batch, const dmpc_opt
                             const float* x_s, const float* theta, const float* x_ref, const float* z_init,
                             const float* lam_init, float* z_out, float* lam_out, int* status_out,
                             int* pcg_iters_out, float* alpha_out);
+
+/* Make (z, lam) with the inputs (x_s, theta, x_ref) the handle's resident solution, as if a
+ * dmpc_solve had returned them: the next dmpc_vjp differentiates at that point (Algorithm 3
+ * linearises at the given z, with lam as the multipliers).  Lets one handle serve several
+ * solves of an autograd graph (a closed-loop rollout): each backward step restores the solution
+ * its forward step returned.  All pointers are device pointers in the dmpc_layout packing,
+ * x_ref may be NULL; lam is the float multiplier output of dmpc_solve.  Stored Schur blocks
+ * (store_schur) are dropped, so the next vjp recomputes them.  Asynchronous on the stream.
+ * Errors: DMPC_E_ARG, DMPC_E_CUDA. */
+dmpc_err dmpc_set_solution(dmpc_handle* h, const float* z, const float* lam, const float* x_s,
+                           const float* theta, const float* x_ref);
 
 /* Change the stream used by later calls. */
 dmpc_err dmpc_set_stream(dmpc_handle* h, void* cuda_stream);

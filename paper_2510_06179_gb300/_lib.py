@@ -21,7 +21,8 @@ class dmpc_options(ctypes.Structure):
     _fields_ = [("sqp_iters", c_int), ("line_search", c_int), ("n_alpha", c_int), ("alpha", c_float * 8),
                 ("ls_eta", c_float), ("feas_tol", c_float), ("pcg_tol", c_float), ("pcg_max_iters", c_int),
                 ("ru_delta", c_float), ("warm_start", c_int), ("store_schur", c_int),
-                ("team_threads", c_int), ("teams_per_block", c_int), ("pcg_precision", c_int)]
+                ("team_threads", c_int), ("teams_per_block", c_int), ("pcg_precision", c_int),
+                ("exact_hessian", c_int)]
 
 
 SIGNATURES = {
@@ -41,6 +42,7 @@ SIGNATURES = {
     "dmpc_inspect_offsets": (c_int, [P, P]),
     "dmpc_solve_noalloc": (c_int, [ctypes.POINTER(dmpc_ocp_desc), c_int, ctypes.POINTER(dmpc_options), P,
                                    P, P, P, P, P, P, P, P, P, P]),
+    "dmpc_set_solution": (c_int, [P, P, P, P, P, P]),
     "dmpc_set_stream": (c_int, [P, P]),
     "dmpc_set_tiling": (c_int, [P, c_int, c_int]),
     "dmpc_get_tiling": (c_int, [P, P, P, P, P]),

@@ -76,6 +76,10 @@ const std::vector<KernelEntry>& registry() {
 }  // namespace
 
 struct dmpc_handle {
+  // pointers already found to be device memory (serving loops pass the same arena pointers
+  // every tick; each cudaPointerGetAttributes costs microseconds of host time)
+  const void* dev_ptr_seen[16] = {};
+  unsigned dev_ptr_next = 0;
   int batch = 0;
   std::vector<dmpc_ocp_desc> descs;
   dmpc_options opt;
@@ -152,6 +156,7 @@ extern "C" void dmpc_default_options(dmpc_options* o) {
   o->team_threads = 0;
   o->teams_per_block = 0;
   o->pcg_precision = 0;
+  o->exact_hessian = 0;
 }
 
 static Options to_kernel_options(const dmpc_options& o) {
@@ -167,6 +172,7 @@ static Options to_kernel_options(const dmpc_options& o) {
   k.pcg_max_iters = o.pcg_max_iters;
   k.ru_delta = o.ru_delta;
   k.pcg_precision = o.pcg_precision;
+  k.exact_hessian = o.exact_hessian;
   return k;
 }
 
@@ -185,6 +191,7 @@ static dmpc_err validate_options(dmpc_handle* h, const dmpc_options& o) {
     return fail(h, DMPC_E_ARG, "team_threads must be 0, 32, 64, 128 or 256");
   if (o.teams_per_block < 0) return fail(h, DMPC_E_ARG, "teams_per_block must be >= 0");
   if (o.pcg_precision != 0 && o.pcg_precision != 1) return fail(h, DMPC_E_ARG, "pcg_precision must be 0 or 1");
+  if (o.exact_hessian != 0 && o.exact_hessian != 1) return fail(h, DMPC_E_ARG, "exact_hessian must be 0 or 1");
   return DMPC_OK;
 }
 
@@ -201,7 +208,7 @@ static dmpc_err configure_tiling(dmpc_handle* h, int team, int tpb) {
     else team = maxK <= 48 ? 32 : (maxK <= 160 ? 64 : (maxK <= 320 ? 128 : 256));
   }
   int ws = 0;
-  for (auto& d : h->descs) ws = std::max(ws, make_layout(d.nx, d.nu, d.T + 1, team).total_floats);
+  for (auto& d : h->descs) ws = std::max(ws, make_layout(d.nx, d.nu, d.T + 1, team, h->opt.exact_hessian).total_floats);
   const size_t ws_bytes = (size_t)ws * sizeof(float);
   const int max_tpb_threads = 256 / team;
   h->use_gws = ws_bytes > (size_t)h->smem_optin;
@@ -396,10 +403,19 @@ static dmpc_err launch(dmpc_handle* h, const KParams& P) {
   return DMPC_OK;
 }
 
+static bool is_device_ptr_seen(dmpc_handle* h, const void* p) {
+  if (!p) return false;
+  for (const void* q : h->dev_ptr_seen)
+    if (q == p) return true;
+  if (!is_device_ptr(p)) return false;
+  h->dev_ptr_seen[h->dev_ptr_next++ % 16] = p;
+  return true;
+}
+
 #define REQUIRE_DEV(ptr, name) \
-  if (!is_device_ptr(ptr)) return fail(h, DMPC_E_ARG, std::string(name) + " must be a device pointer")
+  if (!is_device_ptr_seen(h, ptr)) return fail(h, DMPC_E_ARG, std::string(name) + " must be a device pointer")
 #define OPTIONAL_DEV(ptr, name) \
-  if ((ptr) && !is_device_ptr(ptr)) return fail(h, DMPC_E_ARG, std::string(name) + " must be a device pointer")
+  if ((ptr) && !is_device_ptr_seen(h, ptr)) return fail(h, DMPC_E_ARG, std::string(name) + " must be a device pointer")
 
 extern "C" dmpc_err dmpc_solve(dmpc_handle* h, const float* x_s, const float* theta, const float* x_ref,
                                const float* z_init, const float* lam_init, float* z_out, float* lam_out,
@@ -493,7 +509,7 @@ static const int kPlainPoll = 8;
 static dmpc_err plain_prepare(dmpc_handle* h, KParams* P) {
   const int team = h->team;
   int ws = 0;
-  for (auto& d : h->descs) ws = std::max(ws, make_layout(d.nx, d.nu, d.T + 1, team).total_floats);
+  for (auto& d : h->descs) ws = std::max(ws, make_layout(d.nx, d.nu, d.T + 1, team, h->opt.exact_hessian).total_floats);
   if (!h->plain_ws || ws != h->plain_ws_floats) {
     cudaFree(h->plain_ws);
     h->plain_ws = nullptr;
@@ -654,7 +670,7 @@ extern "C" dmpc_err dmpc_set_ocps(dmpc_handle* h, int n, const int* index, const
     r.p = mi.p_shared + d.T * p_knot(d.model, d.nx, d.nu) + 2 * d.nx + d.nu;
     if (r.n > c.n || r.m > c.m || r.p > c.p || d.nx > c.nx || (long long)K * d.nx > (long long)(c.T + 1) * c.nx ||
         (long long)K * (5 * d.nx * d.nx + d.nx * d.nu) > (long long)(c.T + 1) * (5 * c.nx * c.nx + c.nx * c.nu) ||
-        make_layout(d.nx, d.nu, K, h->team).total_floats > h->max_ws_floats)
+        make_layout(d.nx, d.nu, K, h->team, h->opt.exact_hessian).total_floats > h->max_ws_floats)
       return fail(h, DMPC_E_BUDGET, "shape exceeds the slot's capacity");
     h->recs[b] = r;
     upd[i] = r;
@@ -744,6 +760,38 @@ extern "C" long long dmpc_device_bytes(const dmpc_handle* h) {
   long long b = (long long)h->bytes + (long long)h->gws_floats * (long long)sizeof(float);
   if (h->plain_ws) b += (long long)h->plain_ws_floats * h->batch * (long long)sizeof(float) + (long long)sizeof(PlainState) * h->batch;
   return b;
+}
+
+__global__ void widen_to_double(const float* src, double* dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+
+extern "C" dmpc_err dmpc_set_solution(dmpc_handle* h, const float* z, const float* lam, const float* x_s,
+                                      const float* theta, const float* x_ref) {
+  if (!h) return DMPC_E_ARG;
+  REQUIRE_DEV(z, "z");
+  REQUIRE_DEV(lam, "lam");
+  REQUIRE_DEV(x_s, "x_s");
+  REQUIRE_DEV(theta, "theta");
+  OPTIONAL_DEV(x_ref, "x_ref");
+  const cudaStream_t s = h->stream;
+  cudaError_t e = cudaMemcpyAsync(h->res_z, z, sizeof(float) * h->tot_z, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->res_xs, x_s, sizeof(float) * h->tot_xs, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->res_th, theta, sizeof(float) * h->tot_th, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && x_ref)
+    e = cudaMemcpyAsync(h->res_xref, x_ref, sizeof(float) * h->tot_xref, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_solution copy");
+  if (h->tot_lam > 0) {
+    const int grid = (int)std::min<long long>(4 * (long long)h->n_sm, (h->tot_lam + 255) / 256);
+    widen_to_double<<<grid, 256, 0, s>>>(lam, h->res_lam, h->tot_lam);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_solution kernel");
+  }
+  h->have_solution = true;
+  h->have_store = false;
+  h->last_had_xref = x_ref != nullptr;
+  return DMPC_OK;
 }
 
 extern "C" dmpc_err dmpc_set_stream(dmpc_handle* h, void* s) {

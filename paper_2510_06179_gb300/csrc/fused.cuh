@@ -28,7 +28,7 @@ namespace dmpc {
 
 enum StatusBits : int {
   ST_OK = 0, ST_PCG_MAXITER = 1, ST_NONFINITE = 2, ST_LS_MINSTEP = 4, ST_BAD_INPUT = 8,
-  ST_PCG_BREAKDOWN = 16, ST_CHOL_FAIL = 32, ST_FP64_RESCUE = 64
+  ST_PCG_BREAKDOWN = 16, ST_CHOL_FAIL = 32, ST_FP64_RESCUE = 64, ST_HESS_INDEF = 128
 };
 
 constexpr int kMisc = 256;      // per-team scalars (theta, cost weights, reciprocals)
@@ -36,12 +36,14 @@ constexpr int kRedMax = 48;     // must equal Team<>::RED_MAX
 
 struct Layout {
   int KP;
-  int d_lam, d_lamp, d_gam, d_wx, d_wu, d_r, d_p, d_y, d_total;  // double arrays (in doubles)
+  int d_lam, d_lamp, d_gam, d_wx, d_wu, d_r, d_p, d_y, d_W, d_total;  // double arrays (in doubles)
   int x, u, xp, up, f, C, A, Bm, D, O, Pd, Po, r, p, y, dl, misc, red, bnd, f_total;  // floats
   int total_floats;
 };
 
-__host__ __device__ inline Layout make_layout(int nx, int nu, int K, int team) {
+// exact = 1 adds the exact-Hessian backward's per-knot blocks ((nx+nu)^2 doubles per knot: the
+// Hessian block, then the Riccati factors) and its scratch.
+__host__ __device__ inline Layout make_layout(int nx, int nu, int K, int team, int exact = 0) {
   Layout L;
   L.KP = (K + 1) & ~1;
   const int KP = L.KP;
@@ -54,6 +56,7 @@ __host__ __device__ inline Layout make_layout(int nx, int nu, int K, int team) {
   L.d_r = o; o += nx * KP;
   L.d_p = o; o += nx * KP;
   L.d_y = o; o += nx * KP;
+  L.d_W = o; o += exact ? (nx + nu) * (nx + nu) * (KP + 2) + 2 * (nx + nu) : 0;
   L.d_total = o;
   int f = 2 * o;  // floats start after the doubles
   L.x = f; f += nx * KP;
@@ -100,6 +103,7 @@ struct Ctx {
   double* db;
   float* fb;
   int status;
+  bool exact;  // backward with the exact Hessian of the Lagrangian (Riccati solve), else Gauss-Newton
 
   __device__ __forceinline__ float* F(int off) const { return fb + off; }
   __device__ __forceinline__ double* Dp(int off) const { return db + off; }
@@ -111,6 +115,16 @@ struct Ctx {
   }
   __device__ __forceinline__ double rinv(int i) const {
     return reinterpret_cast<const double*>(fb + L.misc + MS_DINV)[16 + i];
+  }
+  // (vx, vu) = G_k^-1 (wx, wu) over the variables (x_k, u_k) of knot k (u only for k < T),
+  // G_k = diag(Q_k, R) with the projected weights.
+  template <class V>
+  __device__ __forceinline__ void ginv(int k, const V (&wx)[NX], const V (&wu)[NU], double (&vx)[NX],
+                                       double (&vu)[NU]) const {
+#pragma unroll
+    for (int i = 0; i < NX; ++i) vx[i] = (double)wx[i] * qinv(k, i);
+#pragma unroll
+    for (int i = 0; i < NU; ++i) vu[i] = (k < T) ? (double)wu[i] * rinv(i) : 0.0;
   }
   __device__ __forceinline__ float xref(int k, int i) const {
     return P->x_ref ? __ldg(P->x_ref + o.xref_off + (long long)k * NX + i) : 0.f;
@@ -161,26 +175,26 @@ __device__ __forceinline__ void btmv_row(const float* Md, const float* Mo, const
   }
 }
 
-// Inverse of an SPD NX x NX block (Cholesky, then L^-T L^-1).  Returns false if a pivot
-// is not positive (the block is then replaced by the inverse of its diagonal).
-template <int NX>
-__device__ bool spd_inverse(const float* a, float* inv) {
-  float L[NX * NX];
+// Inverse of an SPD NX x NX block (Cholesky, then L^-T L^-1), in float or double.  Returns
+// false if a pivot is not positive (the block is then replaced by the inverse of its diagonal).
+template <int NX, class V = float>
+__device__ bool spd_inverse(const V* a, V* inv) {
+  V L[NX * NX];
 #pragma unroll (NX <= 6 ? 32 : 1)
-  for (int i = 0; i < NX * NX; ++i) L[i] = 0.f;
+  for (int i = 0; i < NX * NX; ++i) L[i] = V(0);
   bool ok = true;
 #pragma unroll (NX <= 6 ? 32 : 1)
   for (int j = 0; j < NX; ++j) {
-    float s = a[j * NX + j];
+    V s = a[j * NX + j];
 #pragma unroll (NX <= 6 ? 32 : 1)
     for (int k = 0; k < j; ++k) s -= L[j * NX + k] * L[j * NX + k];
-    if (!(s > 0.f)) { ok = false; s = fabsf(a[j * NX + j]) + 1e-30f; }
-    float d = sqrtf(s);
+    if (!(s > V(0))) { ok = false; s = fabs(a[j * NX + j]) + V(1e-30); }
+    const V d = sqrt(s);
     L[j * NX + j] = d;
-    float id = 1.f / d;
+    const V id = V(1) / d;
 #pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = j + 1; i < NX; ++i) {
-      float t = a[i * NX + j];
+      V t = a[i * NX + j];
 #pragma unroll (NX <= 6 ? 32 : 1)
       for (int k = 0; k < j; ++k) t -= L[i * NX + k] * L[j * NX + k];
       L[i * NX + j] = t * id;
@@ -188,20 +202,20 @@ __device__ bool spd_inverse(const float* a, float* inv) {
   }
   if (!ok) {
 #pragma unroll (NX <= 6 ? 32 : 1)
-    for (int i = 0; i < NX * NX; ++i) inv[i] = 0.f;
+    for (int i = 0; i < NX * NX; ++i) inv[i] = V(0);
 #pragma unroll (NX <= 6 ? 32 : 1)
-    for (int i = 0; i < NX; ++i) inv[i * NX + i] = 1.f / (fabsf(a[i * NX + i]) + 1e-30f);
+    for (int i = 0; i < NX; ++i) inv[i * NX + i] = V(1) / (fabs(a[i * NX + i]) + V(1e-30));
     return false;
   }
   // W = L^-1 (lower triangular), forward substitution column by column
-  float W[NX * NX];
+  V W[NX * NX];
 #pragma unroll (NX <= 6 ? 32 : 1)
-  for (int i = 0; i < NX * NX; ++i) W[i] = 0.f;
+  for (int i = 0; i < NX * NX; ++i) W[i] = V(0);
 #pragma unroll (NX <= 6 ? 32 : 1)
   for (int c = 0; c < NX; ++c) {
 #pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = c; i < NX; ++i) {
-      float t = (i == c) ? 1.f : 0.f;
+      V t = (i == c) ? V(1) : V(0);
 #pragma unroll (NX <= 6 ? 32 : 1)
       for (int k = c; k < i; ++k) t -= L[i * NX + k] * W[k * NX + c];
       W[i * NX + c] = t / L[i * NX + i];
@@ -212,7 +226,7 @@ __device__ bool spd_inverse(const float* a, float* inv) {
   for (int i = 0; i < NX; ++i) {
 #pragma unroll (NX <= 6 ? 32 : 1)
     for (int j = 0; j <= i; ++j) {
-      float s = 0.f;
+      V s = V(0);
 #pragma unroll (NX <= 6 ? 32 : 1)
       for (int k = (i > j ? i : j); k < NX; ++k) s += W[k * NX + i] * W[k * NX + j];
       inv[i * NX + j] = s;
@@ -387,6 +401,202 @@ __device__ __noinline__ void stage_linearise(Ctx<M, TEAM>& c) {
   c.tm.sync();
 }
 
+// Backward with the exact Hessian of the Lagrangian (Sec. 3.4 contrasts it with the Gauss-
+// Newton matrix the method uses): per knot k < T the block of grad^2_zz L over (x_k, u_k) is
+//   G_k = diag(Q_k, R) - sum_i lambda_{k+1,i} grad^2 Phi_{k,i}(x_k, u_k)   (f_k = x_{k+1} - Phi_k),
+// second derivatives of the integrator step from hyper-dual numbers (one model evaluation per
+// pair of seed directions), lambda from the forward solve; G_T = diag(Q_T).  Stored in FP64
+// at W[(a * NZ + b) * KP + k].
+template <class M, int TEAM>
+__device__ __noinline__ void stage_exact_hessian(Ctx<M, TEAM>& c) {
+  constexpr int NX = M::NX, NU = M::NU, NZ = NX + NU, NP = M::NP;
+  const int T = c.T, KP = c.KP;
+  const float* X = c.F(c.L.x);
+  const float* U = c.F(c.L.u);
+  const double* LAM = c.Dp(c.L.d_lam);
+  double* W = c.Dp(c.L.d_W);
+  if constexpr (!is_lq<M>::value)  // affine dynamics: no curvature (the exact mode is off for LQ)
+  for (int k = c.tm.lane; k < T; k += TEAM) {
+    float lam1[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) lam1[i] = (float)LAM[i * KP + k + 1];
+#pragma unroll 1
+    for (int a = 0; a < NZ; ++a) {
+#pragma unroll 1
+      for (int b = 0; b <= a; ++b) {
+        HDual<1> xh[NX], uh[NU], ph[NP > 0 ? NP : 1], out[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+          xh[i] = HDual<1>(X[i * KP + k]);
+          xh[i].e = (i == a) ? 1.f : 0.f;
+          xh[i].t[0] = (i == b) ? 1.f : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < NU; ++i) {
+          uh[i] = HDual<1>(U[i * KP + k]);
+          uh[i].e = (NX + i == a) ? 1.f : 0.f;
+          uh[i].t[0] = (NX + i == b) ? 1.f : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < NP; ++j) ph[j] = HDual<1>(c.misc(MS_TH + j));
+        model_step<M>(xh, uh, ph, c.dt, out);
+        double h = 0.0;
+#pragma unroll
+        for (int i = 0; i < NX; ++i) h += (double)lam1[i] * (double)out[i].et[0];
+        double g = -h;
+        if (a == b) g += (a < NX) ? (double)c.qproj(k, a) : (double)c.misc(MS_RP + a - NX);
+        W[(a * NZ + b) * KP + k] = g;
+        W[(b * NZ + a) * KP + k] = g;
+      }
+    }
+  }
+  c.tm.sync();
+}
+
+// The exact-Hessian backward KKT system [G H^T; H 0] [z~; lambda~] = [dl/dz; 0] (Eq. 7 with the
+// full G) solved by the discrete-time Riccati recursion in FP64: the per-knot blocks G_k of the
+// Lagrangian Hessian are indefinite for most OCPs away from the pure cost, so H G^-1 H^T is not
+// positive definite and PCG does not apply; the recursion needs only the reduced Hessian to be
+// positive definite (second-order sufficiency at the forward solution).  With the constraint
+// rows x~_{k+1} + A_k x~_k + B_k u~_k = 0, x~_0 = 0 and g = dl/dz:
+//   backward  P_T = G_T, s_T = -g_T;   for k = T-1..0 with Ab = -A_k, Bb = -B_k:
+//     Qxx = G_xx + Ab^T P Ab, Quu = G_uu + Bb^T P Bb, Qux = G_ux + Bb^T P Ab,
+//     qx = -g_x + Ab^T s, qu = -g_u + Bb^T s,  K = -Quu^-1 Qux, k = -Quu^-1 qu,
+//     P_k = Qxx + Qux^T K, s_k = qx + Qux^T k;
+//   forward   u~_k = K x~_k + k, x~_{k+1} = Ab x~_k + Bb u~_k, lambda~_k = -(P_k x~_k + s_k).
+// Knot slot k of W (after its G_k is consumed) holds [P_k | s_k | K_k | k_k].  Writes z~ to
+// (xp, up) and lambda~ to lamp.  A Quu that is not positive definite sets ST_HESS_INDEF.
+template <class M, int TEAM>
+__device__ __noinline__ void stage_riccati_exact(Ctx<M, TEAM>& c) {
+  constexpr int NX = M::NX, NU = M::NU, NZ = NX + NU;
+  constexpr int OP = 0, OS = NX * NX, OK = OS + NX, Ok = OK + NU * NX;  // slot offsets
+  const KParams& P = *c.P;
+  const int T = c.T, KP = c.KP;
+  const float* g = P.dl_dz + c.o.z_off;
+  const float* A = c.F(c.L.A);
+  const float* Bm = c.F(c.L.Bm);
+  double* W = c.Dp(c.L.d_W);
+  double* Q = W + (size_t)NZ * NZ * KP;   // scratch: Q block (NZ x NZ, rows x then u)
+  double* q = Q + NZ * NZ;                // scratch: q (NZ)
+  double* F = q + NZ;                     // scratch: [K | k] (NU x (NX + 1)), then P_k, s_k
+  double* LP = c.Dp(c.L.d_lamp);
+  float* XT = c.F(c.L.xp);
+  float* UT = c.F(c.L.up);
+  const int ln = c.tm.lane;
+  auto slot = [&](int e, int k) -> double& { return W[e * KP + k]; };
+  // P_T, s_T (slot T)
+  for (int e = ln; e < NX * NX; e += TEAM) {
+    const int i = e / NX, j = e % NX;
+    slot(OP + e, T) = (i == j) ? (double)c.qproj(T, i) : 0.0;
+  }
+  for (int i = ln; i < NX; i += TEAM) slot(OS + i, T) = -(double)g[(long long)T * NZ + i];
+  c.tm.sync();
+  for (int k = T - 1; k >= 0; --k) {
+    const int kn = k + 1;  // dynamics step k lives at knot slot k + 1: A_k = A[.., k + 1]
+    // Q = G_k + [Ab Bb]^T P_{k+1} [Ab Bb], q = -g_k + [Ab Bb]^T s_{k+1}
+    for (int e = ln; e < NZ * NZ; e += TEAM) {
+      const int a = e / NZ, b = e % NZ;
+      double acc = W[e * KP + k];
+      for (int i = 0; i < NX; ++i) {
+        const double mi = -(double)(a < NX ? A[(i * NX + a) * KP + kn] : Bm[(i * NU + a - NX) * KP + kn]);
+        double pj = 0.0;
+        for (int j = 0; j < NX; ++j) {
+          const double mj = -(double)(b < NX ? A[(j * NX + b) * KP + kn] : Bm[(j * NU + b - NX) * KP + kn]);
+          pj += slot(OP + i * NX + j, kn) * mj;
+        }
+        acc += mi * pj;
+      }
+      Q[e] = acc;
+    }
+    for (int a = ln; a < NZ; a += TEAM) {
+      double acc = -(double)g[(long long)k * NZ + a];
+      for (int i = 0; i < NX; ++i)
+        acc += -(double)(a < NX ? A[(i * NX + a) * KP + kn] : Bm[(i * NU + a - NX) * KP + kn]) * slot(OS + i, kn);
+      q[a] = acc;
+    }
+    c.tm.sync();
+    // [K | k] = -Quu^-1 [Qux | qu]  (one thread: NU <= 4)
+    if (ln == 0) {
+      double quu[NU * NU], qi[NU * NU];
+#pragma unroll
+      for (int a = 0; a < NU; ++a)
+#pragma unroll
+        for (int b = 0; b < NU; ++b) quu[a * NU + b] = Q[(NX + a) * NZ + NX + b];
+      if (!spd_inverse<NU, double>(quu, qi)) c.status |= ST_HESS_INDEF;
+      for (int a = 0; a < NU; ++a) {
+        for (int j = 0; j <= NX; ++j) {
+          double acc = 0.0;
+          for (int b = 0; b < NU; ++b) acc += qi[a * NU + b] * (j < NX ? Q[(NX + b) * NZ + j] : q[NX + b]);
+          F[a * (NX + 1) + j] = -acc;
+        }
+      }
+    }
+    c.tm.sync();
+    // P_k = Qxx + Qux^T K, s_k = qx + Qux^T k  (into scratch, then into slot k over G_k)
+    double* Pn = F + NU * (NX + 1);
+    for (int e = ln; e < NX * NX + NX; e += TEAM) {
+      const int i = e / NX, j = e % NX;
+      double acc;
+      if (e < NX * NX) {
+        acc = 0.5 * (Q[i * NZ + j] + Q[j * NZ + i]);
+        for (int a = 0; a < NU; ++a)
+          acc += 0.5 * (Q[(NX + a) * NZ + i] * F[a * (NX + 1) + j] + Q[(NX + a) * NZ + j] * F[a * (NX + 1) + i]);
+      } else {
+        const int r = e - NX * NX;
+        acc = q[r];
+        for (int a = 0; a < NU; ++a) acc += Q[(NX + a) * NZ + r] * F[a * (NX + 1) + NX];
+      }
+      Pn[e] = acc;
+    }
+    c.tm.sync();
+    for (int e = ln; e < NX * NX + NX; e += TEAM) slot(OP + e, k) = Pn[e];  // OS = NX * NX follows OP
+    for (int e = ln; e < NU * (NX + 1); e += TEAM) {
+      const int a = e / (NX + 1), j = e % (NX + 1);
+      if (j < NX) slot(OK + a * NX + j, k) = F[e];
+      else slot(Ok + a, k) = F[e];
+    }
+    c.tm.sync();
+  }
+  // forward: x~_0 = 0 (one thread; O(T nz^2))
+  if (ln == 0) {
+    double x[NX], xn[NX], u[NU];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) x[i] = 0.0;
+    for (int k = 0; k <= T; ++k) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        double acc = slot(OS + i, k);
+#pragma unroll
+        for (int j = 0; j < NX; ++j) acc += slot(OP + i * NX + j, k) * x[j];
+        LP[i * KP + k] = -acc;
+        XT[i * KP + k] = (float)x[i];
+      }
+      if (k == T) break;
+#pragma unroll
+      for (int a = 0; a < NU; ++a) {
+        double acc = slot(Ok + a, k);
+#pragma unroll
+        for (int j = 0; j < NX; ++j) acc += slot(OK + a * NX + j, k) * x[j];
+        u[a] = acc;
+        UT[a * KP + k] = (float)acc;
+      }
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < NX; ++j) acc -= (double)A[(i * NX + j) * KP + k + 1] * x[j];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) acc -= (double)Bm[(i * NU + a) * KP + k + 1] * u[a];
+        xn[i] = acc;
+      }
+#pragma unroll
+      for (int i = 0; i < NX; ++i) x[i] = xn[i];
+    }
+  }
+  c.status = c.tm.bor(c.status);
+  c.tm.sync();
+}
+
 // a2: Schur blocks of S_spd = H G^-1 H^T (Eq. 10) in FP32:  D_0 = Q_0^-1,
 // D_k = chi_{k-1} = A Q_{k-1}^-1 A^T + B R^-1 B^T + Q_k^-1,  O_k = phi_{k-1} = A Q_{k-1}^-1.
 // With rhs_from_qp, also gamma_spd = -(d + H G^-1 b) (App. A.2) in FP64.
@@ -554,16 +764,20 @@ __device__ __noinline__ void hp_apply(Ctx<M, TEAM>& c, const double* src, bool r
   }
   c.tm.sync();
   for (int k = c.tm.lane; k < K; k += TEAM) {
-    double s[NX];
+    double s[NX], su[NU], wx[NX], wu[NU];
 #pragma unroll
-    for (int i = 0; i < NX; ++i) s[i] = WX[i * KP + k] * c.qinv(k, i);
+    for (int i = 0; i < NX; ++i) wx[i] = WX[i * KP + k];
+#pragma unroll
+    for (int i = 0; i < NU; ++i) wu[i] = (k < T) ? WU[i * KP + k] : 0.0;
+    c.ginv(k, wx, wu, s, su);
     if (k > 0) {
       const int t = k - 1;
       double vx[NX], vu[NU];
 #pragma unroll
-      for (int j = 0; j < NX; ++j) vx[j] = WX[j * KP + t] * c.qinv(t, j);
+      for (int j = 0; j < NX; ++j) wx[j] = WX[j * KP + t];
 #pragma unroll
-      for (int j = 0; j < NU; ++j) vu[j] = WU[j * KP + t] * c.rinv(j);
+      for (int j = 0; j < NU; ++j) wu[j] = WU[j * KP + t];
+      c.ginv(t, wx, wu, vx, vu);
 #pragma unroll
       for (int i = 0; i < NX; ++i) {
         double acc = s[i];
@@ -1729,17 +1943,23 @@ __device__ __noinline__ void stage_bwd_rhs(Ctx<M, TEAM>& c) {
   const float* Bm = c.F(c.L.Bm);
   double* G = c.Dp(c.L.d_gam);
   double* LP = c.Dp(c.L.d_lamp);
+  const int T = c.T;
   for (int k = c.tm.lane; k < K; k += TEAM) {
-    double s[NX];
+    double s[NX], su[NU];
+    float gx[NX], gu[NU];
 #pragma unroll
-    for (int i = 0; i < NX; ++i) s[i] = (double)g[(long long)k * NZ + i] * c.qinv(k, i);
+    for (int i = 0; i < NX; ++i) gx[i] = g[(long long)k * NZ + i];
+#pragma unroll
+    for (int i = 0; i < NU; ++i) gu[i] = (k < T) ? g[(long long)k * NZ + NX + i] : 0.f;
+    c.ginv(k, gx, gu, s, su);
     if (k > 0) {
       const int t = k - 1;
       double vx[NX], vu[NU];
 #pragma unroll
-      for (int j = 0; j < NX; ++j) vx[j] = (double)g[(long long)t * NZ + j] * c.qinv(t, j);
+      for (int j = 0; j < NX; ++j) gx[j] = g[(long long)t * NZ + j];
 #pragma unroll
-      for (int j = 0; j < NU; ++j) vu[j] = (double)g[(long long)t * NZ + NX + j] * c.rinv(j);
+      for (int j = 0; j < NU; ++j) gu[j] = g[(long long)t * NZ + NX + j];
+      c.ginv(t, gx, gu, vx, vu);
 #pragma unroll
       for (int i = 0; i < NX; ++i) {
 #pragma unroll
@@ -1772,14 +1992,18 @@ __device__ __noinline__ void stage_bwd_finish(Ctx<M, TEAM>& c, int it) {
   const double* WU = c.Dp(c.L.d_wu);
   float* XT = c.F(c.L.xp);
   float* UT = c.F(c.L.up);
-  for (int k = c.tm.lane; k < K; k += TEAM) {
+  for (int k = c.tm.lane; k < K && !c.exact; k += TEAM) {  // exact Hessian: the Riccati solve wrote z~
+    double dx[NX], du[NU], vx[NX], vu[NU];
 #pragma unroll
-    for (int i = 0; i < NX; ++i)
-      XT[i * KP + k] = (float)(((double)g[(long long)k * NZ + i] - WX[i * KP + k]) * c.qinv(k, i));
+    for (int i = 0; i < NX; ++i) dx[i] = (double)g[(long long)k * NZ + i] - WX[i * KP + k];
+#pragma unroll
+    for (int i = 0; i < NU; ++i) du[i] = (k < T) ? (double)g[(long long)k * NZ + NX + i] - WU[i * KP + k] : 0.0;
+    c.ginv(k, dx, du, vx, vu);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) XT[i * KP + k] = (float)vx[i];
     if (k < T) {
 #pragma unroll
-      for (int i = 0; i < NU; ++i)
-        UT[i * KP + k] = (float)(((double)g[(long long)k * NZ + NX + i] - WU[i * KP + k]) * c.rinv(i));
+      for (int i = 0; i < NU; ++i) UT[i * KP + k] = (float)vu[i];
     }
   }
   c.tm.sync();
@@ -1865,6 +2089,13 @@ template <class M, int TEAM>
 __device__ __noinline__ void run_backward(Ctx<M, TEAM>& c) {
   const KParams& P = *c.P;
   stage_load<M, TEAM>(c, true);   // z (returned solution) and lambda (forward multipliers)
+  if (c.exact) {
+    stage_linearise<M, TEAM>(c);
+    stage_exact_hessian<M, TEAM>(c);
+    stage_riccati_exact<M, TEAM>(c);
+    stage_bwd_finish<M, TEAM>(c, 0);
+    return;
+  }
   if (P.store_mode && P.store) {
     store_blocks<M, TEAM>(c, true);
   } else {
@@ -1886,11 +2117,12 @@ __device__ void run_one(const KParams& P, int ocp, float* ws, int lane, int team
   c.T = c.o.T;
   c.K = c.o.T + 1;
   c.dt = c.o.dt;
-  c.L = make_layout(M::NX, M::NU, c.K, TEAM);
+  c.L = make_layout(M::NX, M::NU, c.K, TEAM, P.opt.exact_hessian);
   c.KP = c.L.KP;
   c.db = reinterpret_cast<double*>(ws);
   c.fb = ws;
   c.status = 0;
+  c.exact = !is_lq<M>::value && P.opt.exact_hessian && P.mode == MODE_VJP;
   c.tm.lane = lane;
   c.tm.bar_id = team_in_block + 1;
   c.tm.red = ws + c.L.red;

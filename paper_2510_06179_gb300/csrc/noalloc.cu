@@ -97,7 +97,8 @@ extern "C" dmpc_err dmpc_solve_noalloc(const dmpc_ocp_desc* desc, int batch, con
   if (opt) o = *opt; else dmpc_default_options(&o);
   if (o.sqp_iters < 1 || o.sqp_iters > 1000 || o.n_alpha < 1 || o.n_alpha > 8 || !(o.pcg_tol > 0.f) ||
       !(o.pcg_tol < 1.f) || o.pcg_max_iters < 1 || !(o.ru_delta > 0.f && o.ru_delta < 1.f) ||
-      !(o.ls_eta > 0.f && o.ls_eta < 1.f) || (o.pcg_precision != 0 && o.pcg_precision != 1))
+      !(o.ls_eta > 0.f && o.ls_eta < 1.f) || (o.pcg_precision != 0 && o.pcg_precision != 1) ||
+      (o.exact_hessian != 0 && o.exact_hessian != 1))
     return DMPC_E_ARG;
   for (int i = 0; i < o.n_alpha; ++i)
     if (!(o.alpha[i] > 0.f && o.alpha[i] <= 1.f)) return DMPC_E_ARG;
@@ -122,7 +123,7 @@ extern "C" dmpc_err dmpc_solve_noalloc(const dmpc_ocp_desc* desc, int batch, con
     else team = K <= 48 ? 32 : (K <= 160 ? 64 : (K <= 320 ? 128 : 256));
   }
   if (team != 32 && team != 64 && team != 128 && team != 256) return DMPC_E_ARG;
-  const int ws = make_layout(nx, nu, K, team).total_floats;
+  const int ws = make_layout(nx, nu, K, team, o.exact_hessian).total_floats;
   const size_t ws_bytes = (size_t)ws * sizeof(float);
   const bool use_gws = ws_bytes > (size_t)smem_optin;
   const int max_tpb = 256 / team;
@@ -178,6 +179,7 @@ extern "C" dmpc_err dmpc_solve_noalloc(const dmpc_ocp_desc* desc, int batch, con
   P.opt.pcg_max_iters = o.pcg_max_iters;
   P.opt.ru_delta = o.ru_delta;
   P.opt.pcg_precision = o.pcg_precision;
+  P.opt.exact_hessian = o.exact_hessian;
   P.x_s = x_s; P.theta = theta; P.x_ref = x_ref;
   P.z_init = z_init; P.lam_init_f = lam_init;
   P.z_out = z_out; P.lam_out = lam_out;

@@ -76,10 +76,24 @@ __device__ __noinline__ void plain_step(Ctx<M, TEAM>& c, PlainState& S, int step
   const float* Po = c.F(c.L.Po);
   switch (step) {
     case PS_LOAD: c.status = 0; stage_load<M, TEAM>(c, P.z_init != nullptr); break;
-    case PS_LIN: stage_linearise<M, TEAM>(c); break;
-    case PS_SCHUR: stage_schur<M, TEAM>(c, P.mode != MODE_VJP); break;
-    case PS_PREC: stage_precond<M, TEAM>(c); break;
-    case PS_PCG_SETUP: plain_pcg_setup<M, TEAM>(c, S); break;
+    case PS_LIN:
+      stage_linearise<M, TEAM>(c);
+      if (c.exact) stage_exact_hessian<M, TEAM>(c);
+      break;
+    case PS_SCHUR:  // exact-Hessian backward: the Riccati solve replaces a2-a4
+      if (c.exact) stage_riccati_exact<M, TEAM>(c);
+      else stage_schur<M, TEAM>(c, P.mode != MODE_VJP);
+      break;
+    case PS_PREC:
+      if (!c.exact) stage_precond<M, TEAM>(c);
+      break;
+    case PS_PCG_SETUP:
+      if (c.exact) {
+        if (c.tm.lane == 0) { S.it = 0; S.stall = 0; S.active = 0; S.converged = 1; S.folded = 1; }
+      } else {
+        plain_pcg_setup<M, TEAM>(c, S);
+      }
+      break;
     case PS_MATVEC: {  // y = S p   (Algorithm 4, line 6)
       if (!S.active) break;
       for (int k = c.tm.lane; k < K; k += TEAM) {
@@ -214,7 +228,8 @@ __device__ void plain_one(const KParams& P, PlainState* st, int ocp, int step, i
   c.T = c.o.T;
   c.K = c.o.T + 1;
   c.dt = c.o.dt;
-  c.L = make_layout(M::NX, M::NU, c.K, TEAM);
+  c.L = make_layout(M::NX, M::NU, c.K, TEAM, P.opt.exact_hessian);
+  c.exact = !is_lq<M>::value && P.opt.exact_hessian && P.mode == MODE_VJP;
   c.KP = c.L.KP;
   float* ws = P.gws + (size_t)ocp * P.ws_floats;
   c.db = reinterpret_cast<double*>(ws);

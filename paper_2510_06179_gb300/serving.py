@@ -2,19 +2,21 @@
 
 Requests (one OCP each: model, horizon, x_s, theta, x_ref) arrive over time.  Shapes are
 grouped into classes (model x horizon bucket); each class owns a slot arena (one C-ABI handle
-whose OCPs are slots, sized by the device-memory budget) and a CUDA stream.  Every tick:
+whose OCPs are slots, sized by the device-memory budget) and a CUDA stream.  Every pass of the
+host loop, for each class whose previous tick has finished on the GPU:
 
-  1. admit: arrived requests take free slots of their class (dmpc_set_ocps re-describes the
-     slot and resets its resident iterate; the inputs are scattered into the arena);
-  2. advance: every class with busy slots runs ONE SQP iteration (Algorithm 2) on them with a
-     single subset launch (dmpc_solve_subset, sqp_iters = 1); each slot continues from the
-     iterate it left on the device, so a request admitted now runs alongside requests that
-     are half-way through their solve;
-  3. retire: a request is done after `sqp_iters` ticks; its completion time is the device
-     event of that tick, its solution is gathered from the arena.
+  1. retire: requests whose last SQP iteration ran in that tick are done (completion time =
+     the tick's device event); their slots become free;
+  2. admit: queued requests take free slots (dmpc_set_ocps re-describes the slot and resets its
+     resident iterate; the inputs of all admitted requests are packed into one pinned buffer
+     and scattered into the arena with one copy per array);
+  3. advance: ONE SQP iteration (Algorithm 2) on every busy slot with a single subset launch
+     (dmpc_solve_subset, sqp_iters = 1); each slot continues from the iterate it left on the
+     device, so a request admitted now runs alongside requests half-way through their solve.
 
-Latency = device completion time - host arrival time.  Requests that arrive while a tick is
-on the GPU are admitted at the next tick; the classes' ticks overlap on their streams.
+A class has at most one tick in flight, so requests that arrive while it runs wait at most one
+tick for admission instead of queueing behind launches the GPU has not reached; the classes'
+ticks overlap on their streams.  Latency = device completion time - host arrival time.
 `plain=True` runs the same loop on the plain one-launch-per-step form (dmpc_solve_subset_plain).
 """
 import ctypes
@@ -63,10 +65,17 @@ class SlotClass:
         self.z = torch.zeros(b.n_z, device=device)
         self.lam = torch.zeros(b.n_lam, device=device)
         self.status = torch.zeros(slots, dtype=torch.int32, device=device)
+        # busy-slot list of the tick: pinned staging and device copy, reused (one tick in flight)
+        self.idx_h = torch.zeros(slots, dtype=torch.int32).pin_memory()
+        self.idx_d = torch.zeros(slots, dtype=torch.int32, device=device)
         self.free = deque(range(slots))
-        self.busy = {}              # slot -> (request, ticks done)
+        self.busy = {}              # slot -> [request, ticks launched]
         self.queue = deque()
+        self.inflight = None        # (event, [(slot, request) finishing in that tick])
         self.device = device
+
+    def idle(self):
+        return self.inflight is None or self.inflight[0].query()
 
     def admit(self):
         """Move queued requests into free slots; upload their inputs and shapes."""
@@ -85,35 +94,32 @@ class SlotClass:
             descs[i] = _lib.dmpc_ocp_desc(MODEL_IDS[r.model], r.nx, r.nu, r.T, r.dt)
         reset = np.ones(len(new), dtype=np.int32)
         with torch.cuda.stream(self.stream):
-            # inputs: pack on the host, one copy per array, scatter on the device
-            xs_h = np.concatenate([r.x_s for _, r in new])
-            th_h = np.concatenate([r.theta for _, r in new])
-            xr_h = np.concatenate([r.x_ref.ravel() for _, r in new])
-            xs_d = torch.from_numpy(xs_h).pin_memory().to(self.device, non_blocking=True)
-            th_d = torch.from_numpy(th_h).pin_memory().to(self.device, non_blocking=True)
-            xr_d = torch.from_numpy(xr_h).pin_memory().to(self.device, non_blocking=True)
-            oxs = oth = oxr = 0
-            for s, r in new:
-                n_xs, n_th, n_xr = r.nx, r.theta.size, r.x_ref.size
-                self.x_s[b.xs_off[s]:b.xs_off[s] + n_xs].copy_(xs_d[oxs:oxs + n_xs], non_blocking=True)
-                self.theta[b.th_off[s]:b.th_off[s] + n_th].copy_(th_d[oth:oth + n_th], non_blocking=True)
-                self.x_ref[b.xref_off[s]:b.xref_off[s] + n_xr].copy_(xr_d[oxr:oxr + n_xr], non_blocking=True)
-                oxs += n_xs; oth += n_th; oxr += n_xr
+            # values of all admitted requests and their arena positions, one scatter per array
+            for arena, off, field in ((self.x_s, b.xs_off, "x_s"), (self.theta, b.th_off, "theta"),
+                                      (self.x_ref, b.xref_off, "x_ref")):
+                vals = np.concatenate([getattr(r, field).reshape(-1) for _, r in new]).astype(np.float32)
+                pos = np.concatenate([np.arange(off[s], off[s] + getattr(r, field).size, dtype=np.int64)
+                                      for s, r in new])
+                v_d = torch.from_numpy(vals).pin_memory().to(self.device, non_blocking=True)
+                p_d = torch.from_numpy(pos).pin_memory().to(self.device, non_blocking=True)
+                arena.index_copy_(0, p_d, v_d)
             _lib.check(self.lib.dmpc_set_ocps(b.h, len(new), idx.ctypes.data_as(ctypes.c_void_p),
                                               descs, reset.ctypes.data_as(ctypes.c_void_p)), b.h)
         return len(new)
 
     def advance(self, plain):
-        """One SQP iteration on every busy slot (one launch); returns (event, slots done)."""
+        """One SQP iteration on every busy slot (one launch); records the tick in flight."""
         if not self.busy:
-            return None, []
+            return False
         b = self.batch
         slots = np.fromiter(self.busy.keys(), dtype=np.int32)
+        n = slots.size
         with torch.cuda.stream(self.stream):
-            idx = torch.from_numpy(slots).pin_memory().to(self.device, non_blocking=True)
+            self.idx_h[:n].copy_(torch.from_numpy(slots))
+            self.idx_d[:n].copy_(self.idx_h[:n], non_blocking=True)
             fn = self.lib.dmpc_solve_subset_plain if plain else self.lib.dmpc_solve_subset
             ptr = lambda t: ctypes.c_void_p(t.data_ptr())
-            _lib.check(fn(b.h, ptr(idx), len(slots), ptr(self.x_s), ptr(self.theta), ptr(self.x_ref), ptr(self.z),
+            _lib.check(fn(b.h, ptr(self.idx_d), n, ptr(self.x_s), ptr(self.theta), ptr(self.x_ref), ptr(self.z),
                           ptr(self.lam), ptr(self.status), None, None), b.h)
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(self.stream)
@@ -123,9 +129,16 @@ class SlotClass:
             st[1] += 1
             if st[1] >= b.sqp_iters_total:
                 done.append((s, self.busy.pop(s)[0]))   # not advanced again; freed when retired
-        return ev, done
+        self.inflight = (ev, done)
+        return True
 
-    def retire(self, done, t_done, keep_solution):
+    def retire(self, start_ev, keep_solution):
+        """Finish the tick in flight (its event has completed); returns the requests done."""
+        if self.inflight is None:
+            return 0
+        ev, done = self.inflight
+        self.inflight = None
+        t_done = start_ev.elapsed_time(ev) / 1e3
         b = self.batch
         for s, r in done:
             r.done = t_done
@@ -134,6 +147,7 @@ class SlotClass:
                 r.z = self.z[b.z_off[s]:b.z_off[s] + n].detach().cpu().numpy().copy()
                 r.status = int(self.status[s].item())
             self.free.append(s)
+        return len(done)
 
 
 class ServingEngine:
@@ -172,7 +186,6 @@ class ServingEngine:
     def run(self, requests, keep_solutions=False, max_seconds=60.0):
         """Serve `requests` (sorted by arrival); returns the list with done times filled."""
         pending = deque(sorted(requests, key=lambda r: r.arrival))
-        inflight = deque()          # (event, class, slots)
         torch.cuda.synchronize(self.device)
         start_ev = torch.cuda.Event(enable_timing=True)
         start_ev.record(torch.cuda.current_stream(self.device))
@@ -180,6 +193,7 @@ class ServingEngine:
         t0 = time.perf_counter()
         n_done = 0
         total = len(pending)
+        classes = list(self.classes.values())
         while n_done < total:
             now = time.perf_counter() - t0
             if now > max_seconds:
@@ -187,29 +201,20 @@ class ServingEngine:
             while pending and pending[0].arrival <= now:
                 r = pending.popleft()
                 self.class_of(r).queue.append(r)
-            for c in self.classes.values():
+            active = False
+            for c in classes:
+                if not c.idle():
+                    active = True
+                    continue
+                n_done += c.retire(start_ev, keep_solutions)
                 c.admit()
-            launched = False
-            for c in self.classes.values():
-                ev, done = c.advance(self.plain)
-                if ev is not None:
-                    inflight.append((ev, c, done))
-                    launched = True
-            # retire finished ticks (in order per class stream; events are queried, not waited on)
-            while inflight and (inflight[0][0].query() or not launched):
-                ev, c, done = inflight.popleft()
-                ev.synchronize()
-                t_done = start_ev.elapsed_time(ev) / 1e3
-                if done:
-                    c.retire(done, t_done, keep_solutions)
-                    n_done += len(done)
-            if not launched and not inflight and pending:
+                active = c.advance(self.plain) or active
+            if not active and pending:
                 time.sleep(max(0.0, min(1e-4, pending[0].arrival - (time.perf_counter() - t0))))
-        while inflight:
-            ev, c, done = inflight.popleft()
-            ev.synchronize()
-            if done:
-                c.retire(done, start_ev.elapsed_time(ev) / 1e3, keep_solutions)
+        for c in classes:
+            if c.inflight is not None:
+                c.inflight[0].synchronize()
+                c.retire(start_ev, keep_solutions)
         return requests
 
     def close(self):

@@ -77,6 +77,8 @@ class OCPBatch:
         self.z_off, self.lam_off, self.th_off, self.xs_off, self.xref_off = offs
         self.n_z, self.n_lam, self.n_th, self.n_xs, self.n_xref = (int(o[-1]) for o in offs)
         self.sqp_iters = self.options.sqp_iters
+        self.generation = 0         # id of the solve whose solution is resident on the device
+        self._next_generation = 1
 
     # ------------------------------------------------------------------------------
     def _alloc(self, n, dtype=torch.float32):
@@ -106,7 +108,26 @@ class OCPBatch:
         code = fn(self.h, _ptr(x_s), _ptr(theta), _ptr(x_ref), _ptr(z_init), _ptr(lam_init),
                   _ptr(z), _ptr(lam), _ptr(st), _ptr(it), _ptr(al))
         _lib.check(code, self.h)
+        self.generation = self._next_generation
+        self._next_generation += 1
         return dict(z=z, lam=lam, status=st, pcg_iters=it, alpha=al)
+
+    def set_solution(self, z, lam, x_s, theta, x_ref=None, generation=None):
+        """Make (z, lam) at inputs (x_s, theta, x_ref) the resident solution (dmpc_set_solution),
+        so the next vjp differentiates there; `generation` names the solve it came from."""
+        d = self.device
+        _dev_f32(z, self.n_z, "z", d)
+        _dev_f32(lam, self.n_lam, "lam", d)
+        _dev_f32(x_s, self.n_xs, "x_s", d)
+        _dev_f32(theta, self.n_th, "theta", d)
+        _dev_f32(x_ref, self.n_xref, "x_ref", d)
+        self._set_stream()
+        _lib.check(self.lib.dmpc_set_solution(self.h, _ptr(z), _ptr(lam), _ptr(x_s), _ptr(theta), _ptr(x_ref)),
+                   self.h)
+        if generation is None:
+            generation = self._next_generation
+            self._next_generation += 1
+        self.generation = generation
 
     def vjp(self, dl_dz, out=None, want_stats=True, plain=False):
         """Backward pass at the last solution.  Returns dict(dtheta, dxs, lamt, status, pcg_iters).
@@ -181,21 +202,28 @@ class OCPBatch:
 class DiffMPCFunction(torch.autograd.Function):
     """z = solve(x_s, theta); backward: the adjoint PCG + theta contraction (Algorithm 3).
 
-    The OCPBatch keeps the solution resident on the device; x_s, theta and x_ref are kept
-    alive by the autograd graph until backward runs."""
+    The OCPBatch keeps the latest solution resident on the device.  When the same batch solved
+    again after this call (several solves in one graph, e.g. a closed-loop rollout), backward
+    first restores this call's solution and inputs with set_solution."""
 
     @staticmethod
     def forward(ctx, x_s, theta, batch, x_ref=None, z_init=None):
-        out = batch.solve(x_s.detach().contiguous(), theta.detach().contiguous(),
-                          None if x_ref is None else x_ref.detach().contiguous(), z_init, want_stats=False)
+        xs_d, th_d = x_s.detach().contiguous(), theta.detach().contiguous()
+        xr_d = None if x_ref is None else x_ref.detach().contiguous()
+        out = batch.solve(xs_d, th_d, xr_d, z_init, want_stats=False)
         ctx.batch = batch
-        ctx.keep = (x_s, theta, x_ref)
+        ctx.generation = batch.generation
+        ctx.inputs = (xs_d, th_d, xr_d)
+        ctx.solution = (out["z"], out["lam"])
         ctx.mark_non_differentiable(out["lam"])
         return out["z"], out["lam"]
 
     @staticmethod
     def backward(ctx, grad_z, grad_lam):
-        res = ctx.batch.vjp(grad_z.contiguous(), want_stats=False)
+        b = ctx.batch
+        if b.generation != ctx.generation:
+            b.set_solution(*ctx.solution, *ctx.inputs, generation=ctx.generation)
+        res = b.vjp(grad_z.contiguous(), want_stats=False)
         return res["dxs"], res["dtheta"], None, None, None
 
 

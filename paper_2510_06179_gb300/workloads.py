@@ -143,6 +143,55 @@ def lq_config(B=16, T=20, nx=4, nu=1, seed=0, c_var=0.0):
                     sqp_iters=1, line_search=False, pcg_tol=1e-8, u_target=_f32(u_t))
 
 
+# Closed-loop RL benchmark problems (App. B.1, RL timing table): (nx, nu, MPC horizon T,
+# episode length H, batch B).
+RL_PROBLEMS = {1: (8, 4, 40, 50, 64), 2: (8, 4, 30, 50, 16), 3: (8, 4, 30, 50, 64), 4: (8, 4, 30, 50, 256),
+               5: (16, 8, 30, 50, 16), 6: (16, 8, 30, 50, 64)}
+
+
+@dataclass
+class RLProblem:
+    """A batch of random LQ environments x_{h+1} = A x_h + B u_h + b with an MPC policy whose
+    cost is x^T diag(q) x + ||u||^2 over horizon T (the learned parameters are q)."""
+    nx: int
+    nu: int
+    T: int
+    H: int
+    A: np.ndarray       # (B, nx, nx) float32
+    Bm: np.ndarray      # (B, nx, nu) float32
+    b: np.ndarray       # (B, nx) float32
+    x0: np.ndarray      # (B, nx) float32
+    q0: np.ndarray      # (B, nx) float32 initial diag(Q)
+
+    @property
+    def B(self):
+        return self.x0.shape[0]
+
+    def knot_theta(self):
+        """Per-knot LQ parameters (A, B, b) of the MPC model, repeated over the horizon."""
+        k = np.concatenate([self.A.reshape(self.B, -1), self.Bm.reshape(self.B, -1), self.b], axis=1)
+        return _f32(np.repeat(k[:, None, :], self.T, axis=1).reshape(self.B, -1))
+
+
+def rl_lq_problem(problem=1, seed=0, B=None, H=None, T=None):
+    """Random LQ problem of the RL benchmark: A = I + 0.1 dA, vec(dA) ~ N(0, I), eigenvalues
+    clipped to modulus <= 0.99 (phases kept); vec(B) ~ N(0, I); b ~ N(0, 1e-4 I); x_0 ~ N(0, 25 I).
+    Initial cost weights diag(Q) ~ U[0.5, 2] (the paper does not state them).  B, H, T override
+    the table's sizes."""
+    nx, nu, T0, H0, B0 = RL_PROBLEMS[problem]
+    B, H, T = B or B0, H or H0, T or T0
+    rng = np.random.default_rng(seed)
+    A = np.eye(nx) + 0.1 * rng.standard_normal((B, nx, nx))
+    lam, V = np.linalg.eig(A)
+    lam = lam * np.minimum(1.0, 0.99 / np.maximum(np.abs(lam), 1e-300))
+    A = np.real(V @ (lam[..., None] * np.linalg.inv(V)))
+    Bm = rng.standard_normal((B, nx, nu))
+    b = 1e-2 * rng.standard_normal((B, nx))
+    x0 = 5.0 * rng.standard_normal((B, nx))
+    q0 = rng.uniform(0.5, 2.0, size=(B, nx))
+    return RLProblem(nx, nu, T, H, _f32(A), _f32(Bm), _f32(b), _f32(x0), _f32(q0))
+
+
 def cartpole_config(B=256, T=50, seed=0, sqp_iters=10, pcg_tol=1e-6, dt=0.05):
     """Cart-pole swing-up/balance: m_p ~ U[0.05, 0.2], L ~ U[0.3, 0.7], diag Q ~ U[0.1, 10],
     diag R ~ U[0.01, 1], Q_T = 10 Q; x_0: angle ~ U[-pi, pi], other states ~ N(0, 0.5);
