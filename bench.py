@@ -83,7 +83,7 @@ def throughput(world, steps, seconds):
 # dram__bytes_read.sum + dram__bytes_write.sum of one forward launch from an ncu capture of this
 # bench step (the command and counters are summarised under profiles/), with the hash of the
 # kernel sources it was taken on; reported only while the sources still hash the same.
-TRAFFIC_CAPTURE = {"src_sha256_16": "350e556c4b1620df", "bytes_per_launch": 673792 + 145920}
+TRAFFIC_CAPTURE = {"src_sha256_16": "2f927747e2c8a302", "bytes_per_launch": 691712 + 144896}
 
 
 def kernel_source_hash():
@@ -502,6 +502,26 @@ def suite(path):
     dl = torch.zeros_like(z)
     dl.view(1024, -1)[:, 6] = 1.0
     out["vehicle_b1024"] = _fused_vs_plain(b, inp, dl, 3, 1024)
+    # one training step of the learned cost weights: features -> MLP -> theta -> solve -> loss
+    # -> backward through the solve and the MLP -> optimizer step
+    from paper_2510_06179_gb300.cost_mlp import CostMLP, vehicle_theta
+    from paper_2510_06179_gb300.solver import DiffMPCFunction
+    mlp = CostMLP().to(dev)
+    opt = torch.optim.Adam(mlp.parameters(), lr=1e-3)
+    feats, shared = t(w.extra["features"]).view(1024, 16), t(w.theta[:, :2]).view(1024, 2)
+    x_s, x_ref = inp[0], inp[2]
+
+    def train_step():
+        q, r = mlp(feats)
+        zz, _ = DiffMPCFunction.apply(x_s, vehicle_theta(shared, q, r), b, x_ref, None)
+        u0 = zz.view(1024, -1)[:, 6:8]
+        loss = (u0[:, 0] ** 2).sum() + 1e-6 * (u0[:, 1] ** 2).sum()
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+
+    tm, tm_wall = _timed(train_step, 3, warm=1)
+    out["vehicle_b1024"]["mlp_train_step_ms"] = max(tm, tm_wall) * 1e3
     b.close()
 
     # attitude stabilisation (App. B.1): 16 OCPs, nx = nu = 3, Euler dt 0.1, T = 25; forward alone
