@@ -570,6 +570,9 @@ def suite(path):
     for plain in (False, True):
         eng = ServingEngine(workloads.SERVING_SHAPES, budget_bytes=64 << 30, sqp_iters=5, slots_per_class=512,
                             plain=plain, pcg_tol=PCG_TOL)
+        # warm-up pass (first launches of every class, pinned-memory pools), not reported
+        warm = [Request(rid=i, **d) for i, d in enumerate(workloads.serving_trace(1000, 0.3, seed=1))]
+        eng.run(warm, max_seconds=30.0)
         rows = {}
         for rate in (1000, 5000, 10000, 20000, 50000):
             dur = min(1.0, 20000 / rate)

@@ -2,8 +2,9 @@
 // floats with |lo| <= ulp(hi)/2, giving about 48 significant bits with FP32 instructions only.
 // Built from the error-free transformations TwoSum (Knuth) and TwoProd (with a fused
 // multiply-add); used where FP64 would otherwise be needed in an inner loop, since FP64 runs
-// at 1/64 of the FP32 rate on this GPU.  No operation here may be re-associated: the file is
-// compiled without fast-math, and the sums contain no products the compiler could contract.
+// at 1/64 of the FP32 rate on this GPU.  No operation here may be re-associated or contracted:
+// the file is compiled without fast-math, and every product whose rounding matters is an
+// explicitly rounded multiply (__fmul_rn), which the compiler never fuses into an addition.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -35,7 +36,7 @@ __device__ __forceinline__ dfl quick_two_sum(float a, float b) {
 }
 // p + e = a * b exactly
 __device__ __forceinline__ dfl two_prod(float a, float b) {
-  const float p = a * b;
+  const float p = __fmul_rn(a, b);
   const float e = fmaf(a, b, -p);
   return {p, e};
 }
@@ -68,6 +69,41 @@ __device__ __forceinline__ dfl df_div(dfl a, dfl b) {
   const float q2 = r.hi / b.hi;
   return quick_two_sum(q1, q2);
 }
+
+// Compensated accumulation, the Dot2 scheme of Ogita, Rump and Oishi (2005): s is the running
+// FP32 sum and c collects the exact rounding error of every addition (TwoSum) and product
+// (TwoProd) together with the low-order cross products, so s + c is as accurate as a sum carried
+// in twice the precision and then rounded.  The dependent chain per term is one addition on s,
+// with the error terms hanging off it, instead of the renormalising double-float addition.
+struct dacc {
+  float s, c;
+};
+__device__ __forceinline__ dacc dacc_zero() { return {0.f, 0.f}; }
+__device__ __forceinline__ void dacc_add(dacc& a, float x) {
+  const float t = a.s + x;
+  const float z = t - a.s;
+  a.c += (a.s - (t - z)) + (x - z);
+  a.s = t;
+}
+__device__ __forceinline__ void dacc_add(dacc& a, dfl x) {
+  dacc_add(a, x.hi);
+  a.c += x.lo;
+}
+// a += m * v, m a float
+__device__ __forceinline__ void dacc_fma(dacc& a, float m, dfl v) {
+  const float p = __fmul_rn(m, v.hi);
+  const float e = fmaf(m, v.hi, -p);
+  dacc_add(a, p);
+  a.c += fmaf(m, v.lo, e);
+}
+// a += u * v, both double-float (u.lo * v.lo is below the precision kept)
+__device__ __forceinline__ void dacc_fma(dacc& a, dfl u, dfl v) {
+  const float p = __fmul_rn(u.hi, v.hi);
+  const float e = fmaf(u.hi, v.hi, -p);
+  dacc_add(a, p);
+  a.c += fmaf(u.hi, v.lo, fmaf(u.lo, v.hi, e));
+}
+__device__ __forceinline__ dfl dacc_get(const dacc& a) { return two_sum(a.s, a.c); }
 
 // Sum over a warp (butterfly; every lane gets the same value).
 __device__ __forceinline__ dfl df_warp_sum(dfl v) {

@@ -147,7 +147,7 @@ __device__ __forceinline__ float blk(const float* base, int KP, int k, int i, in
 }
 
 // out = Md_k v_k + Mo_k v_{k-1} + Mo_{k+1}^T v_{k+1}  (symmetric block-tridiagonal row k);
-// FP32 blocks, vectors and accumulation in V (float, or double for the FP64 rescue path).
+// FP32 blocks, vectors and accumulation in V.
 template <int NX, class V>
 __device__ __forceinline__ void btmv_row(const float* Md, const float* Mo, const V* v, int k, int K,
                                          int KP, V* out) {
@@ -804,77 +804,185 @@ __device__ __forceinline__ void hp_residual(Ctx<M, TEAM>& c, const double* src) 
   hp_apply<M, TEAM>(c, src, true, nullptr);
 }
 
-// FP64 rescue of a PCG solve (Algorithm 4 with the operator S applied in FP64 from the
-// factors, the preconditioner blocks in FP32, vectors and sums in FP64), continuing from
-// lamp.  Used for the OCPs whose FP32 inner iteration stagnated or broke down.
+// Double-float rescue for any team size (workspace vectors): Algorithm 4 continued from the
+// folded solution with the vectors, the scalars and every sum in double-float (compensated
+// accumulation, FP32 instructions), the operator S = H G^-1 H^T applied from the FP32 factors
+// and the reciprocal weights (the FP64 true-residual operator), and the preconditioner from its
+// FP32 blocks (exactly symmetric: the diagonal blocks are formed symmetric).  Replaces an FP64
+// rescue whose cost on this GPU's FP64 pipe dominated large OCPs.  Vectors live in the double
+// arrays of the workspace, one (hi, lo) pair per double slot.
+template <int TEAM>
+__device__ __forceinline__ dfl team_df_sum(Team<TEAM>& tm, dfl v) {
+  v = df_warp_sum(v);
+  if (TEAM <= 32) {
+    __syncwarp();
+    return v;
+  }
+  constexpr int NW = TEAM / 32, RM = Team<TEAM>::RED_MAX;
+  float* rb = tm.red + tm.buf * (NW * RM);
+  const int w = tm.lane >> 5;
+  if ((tm.lane & 31) == 0) { rb[w * RM] = v.hi; rb[w * RM + 1] = v.lo; }
+  tm.sync();
+  dfl s = {rb[0], rb[1]};
+  for (int q = 1; q < NW; ++q) s = df_add(s, dfl{rb[q * RM], rb[q * RM + 1]});
+  tm.buf ^= 1;
+  return s;
+}
+
+// out = S v in double-float; leaves w = H^T v in (WX, WU).
 template <class M, int TEAM>
-__device__ __noinline__ int stage_pcg64(Ctx<M, TEAM>& c, double eta0, int maxit) {
-  constexpr int NX = M::NX;
+__device__ __noinline__ void df_apply(Ctx<M, TEAM>& c, const dfl* v, dfl* out, dfl* WX, dfl* WU,
+                                      const dfl (&qx)[M::NX], const dfl (&qT)[M::NX], const dfl (&ri)[M::NU]) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const int T = c.T, K = c.K, KP = c.KP;
+  const float* A = c.F(c.L.A);
+  const float* Bm = c.F(c.L.Bm);
+  c.tm.sync();
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+#pragma unroll (NX <= 6 ? 32 : 1)
+    for (int i = 0; i < NX; ++i) {
+      dacc a = dacc_zero();
+      dacc_add(a, v[i * KP + k]);
+      if (k < T) {
+#pragma unroll
+        for (int j = 0; j < NX; ++j) dacc_fma(a, A[(j * NX + i) * KP + k + 1], v[j * KP + k + 1]);
+      }
+      WX[i * KP + k] = dacc_get(a);
+    }
+    if (k < T) {
+#pragma unroll
+      for (int i = 0; i < NU; ++i) {
+        dacc a = dacc_zero();
+#pragma unroll
+        for (int j = 0; j < NX; ++j) dacc_fma(a, Bm[(j * NU + i) * KP + k + 1], v[j * KP + k + 1]);
+        WU[i * KP + k] = dacc_get(a);
+      }
+    }
+  }
+  c.tm.sync();
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    dfl vx[NX], vu[NU];
+    if (k > 0) {
+#pragma unroll
+      for (int j = 0; j < NX; ++j) vx[j] = df_mul(WX[j * KP + k - 1], qx[j]);  // k - 1 < T
+#pragma unroll
+      for (int j = 0; j < NU; ++j) vu[j] = df_mul(WU[j * KP + k - 1], ri[j]);
+    }
+#pragma unroll (NX <= 6 ? 32 : 1)
+    for (int i = 0; i < NX; ++i) {
+      dacc a = dacc_zero();
+      dacc_add(a, df_mul(WX[i * KP + k], k < T ? qx[i] : qT[i]));
+      if (k > 0) {
+#pragma unroll
+        for (int j = 0; j < NX; ++j) dacc_fma(a, A[(i * NX + j) * KP + k], vx[j]);
+#pragma unroll
+        for (int j = 0; j < NU; ++j) dacc_fma(a, Bm[(i * NU + j) * KP + k], vu[j]);
+      }
+      out[i * KP + k] = dacc_get(a);
+    }
+  }
+  c.tm.sync();
+}
+
+template <int NX>
+__device__ __forceinline__ void btmv_row_df(const float* Md, const float* Mo, const dfl* v, int k, int K, int KP,
+                                            dfl (&out)[NX]) {
+#pragma unroll (NX <= 6 ? 32 : 1)
+  for (int i = 0; i < NX; ++i) {
+    dacc a = dacc_zero();
+#pragma unroll
+    for (int j = 0; j < NX; ++j) dacc_fma(a, Md[(i * NX + j) * KP + k], v[j * KP + k]);
+    if (k > 0) {
+#pragma unroll
+      for (int j = 0; j < NX; ++j) dacc_fma(a, Mo[(i * NX + j) * KP + k], v[j * KP + k - 1]);
+    }
+    if (k + 1 < K) {
+#pragma unroll
+      for (int j = 0; j < NX; ++j) dacc_fma(a, Mo[(j * NX + i) * KP + k + 1], v[j * KP + k + 1]);
+    }
+    out[i] = dacc_get(a);
+  }
+}
+
+template <class M, int TEAM>
+__device__ __noinline__ int stage_pcg_df(Ctx<M, TEAM>& c, float eta0f, int maxit) {
+  constexpr int NX = M::NX, NU = M::NU;
   const KParams& P = *c.P;
   const int K = c.K, KP = c.KP;
   const float* Pd = c.F(c.L.Pd);
   const float* Po = c.F(c.L.Po);
   double* LP = c.Dp(c.L.d_lamp);
-  double* Rv = c.Dp(c.L.d_r);
-  double* Pv = c.Dp(c.L.d_p);
-  double* Y = c.Dp(c.L.d_y);
   const double* G = c.Dp(c.L.d_gam);
-  const double tol2 = (double)P.opt.pcg_tol * (double)P.opt.pcg_tol;
-  float* Rf = c.F(c.L.r);  // FP32 copy of the residual for the (FP32) preconditioner
-  hp_apply<M, TEAM>(c, LP, false, Y);
+  // double-float vectors: x in d_y, r in d_r, p in d_p (one pair per double slot); y = S p in
+  // the FP32 scratch arrays r and p, which are contiguous (2 NX KP floats = NX KP pairs)
+  dfl* X = reinterpret_cast<dfl*>(c.Dp(c.L.d_y));
+  dfl* R = reinterpret_cast<dfl*>(c.Dp(c.L.d_r));
+  dfl* Pv = reinterpret_cast<dfl*>(c.Dp(c.L.d_p));
+  dfl* Y = reinterpret_cast<dfl*>(c.F(c.L.r));  // spans the FP32 arrays r and p (contiguous)
+  dfl* WX = reinterpret_cast<dfl*>(c.Dp(c.L.d_wx));
+  dfl* WU = reinterpret_cast<dfl*>(c.Dp(c.L.d_wu));
+  dfl qx[NX], qT[NX], ri[NU];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) { qx[i] = df_from(c.qinv(0, i)); qT[i] = df_from(c.qinv(c.T, i)); }
+#pragma unroll
+  for (int i = 0; i < NU; ++i) ri[i] = df_from(c.rinv(i));
+  const dfl thr = df_mulf(df_make(eta0f), P.opt.pcg_tol * P.opt.pcg_tol);
   for (int k = c.tm.lane; k < K; k += TEAM)
 #pragma unroll
-    for (int i = 0; i < NX; ++i) {
-      Rv[i * KP + k] = G[i * KP + k] - Y[i * KP + k];
-      Rf[i * KP + k] = (float)Rv[i * KP + k];
-    }
-  c.tm.sync();
-  double e[1] = {0.0};
-  for (int k = c.tm.lane; k < K; k += TEAM) {
-    float z[NX];
-    btmv_row<NX>(Pd, Po, Rf, k, K, KP, z);
+    for (int i = 0; i < NX; ++i) X[i * KP + k] = df_from(LP[i * KP + k]);
+  df_apply<M, TEAM>(c, X, Pv, WX, WU, qx, qT, ri);  // Pv = S x (temporarily)
+  for (int k = c.tm.lane; k < K; k += TEAM)
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { Pv[i * KP + k] = (double)z[i]; e[0] += Rv[i * KP + k] * (double)z[i]; }
+    for (int i = 0; i < NX; ++i) R[i * KP + k] = df_sub(df_from(G[i * KP + k]), Pv[i * KP + k]);
+  c.tm.sync();
+  dacc ea = dacc_zero();
+  for (int k = c.tm.lane; k < K; k += TEAM) {
+    dfl z[NX];
+    btmv_row_df<NX>(Pd, Po, R, k, K, KP, z);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { Pv[i * KP + k] = z[i]; dacc_fma(ea, R[i * KP + k], z[i]); }
   }
-  c.tm.sum(e);
-  double eta = e[0];
+  dfl eta = team_df_sum<TEAM>(c.tm, dacc_get(ea));
   int it = 0;
-  bool converged = !(eta > tol2 * eta0);
+  bool converged = !(eta.hi > thr.hi);
   while (!converged && it < maxit) {
-    hp_apply<M, TEAM>(c, Pv, false, Y);
-    double v[1] = {0.0};
+    df_apply<M, TEAM>(c, Pv, Y, WX, WU, qx, qT, ri);
+    dacc va = dacc_zero();
     for (int k = c.tm.lane; k < K; k += TEAM)
 #pragma unroll
-      for (int i = 0; i < NX; ++i) v[0] += Pv[i * KP + k] * Y[i * KP + k];
-    c.tm.sum(v);
-    if (!(v[0] > 0.0) || !isfinite(v[0])) { c.status |= ST_PCG_BREAKDOWN; break; }
-    const double alpha = eta / v[0];
+      for (int i = 0; i < NX; ++i) dacc_fma(va, Pv[i * KP + k], Y[i * KP + k]);
+    const dfl v = team_df_sum<TEAM>(c.tm, dacc_get(va));
+    if (!(v.hi > 0.f) || !isfinite(v.hi)) { c.status |= ST_PCG_BREAKDOWN; break; }
+    const dfl alpha = df_div(eta, v);
     for (int k = c.tm.lane; k < K; k += TEAM)
 #pragma unroll
       for (int i = 0; i < NX; ++i) {
-        LP[i * KP + k] += alpha * Pv[i * KP + k];
-        Rv[i * KP + k] -= alpha * Y[i * KP + k];
-        Rf[i * KP + k] = (float)Rv[i * KP + k];
+        X[i * KP + k] = df_add(X[i * KP + k], df_mul(alpha, Pv[i * KP + k]));
+        R[i * KP + k] = df_sub(R[i * KP + k], df_mul(alpha, Y[i * KP + k]));
       }
     c.tm.sync();
-    double e1[1] = {0.0};
+    dacc na = dacc_zero();
     for (int k = c.tm.lane; k < K; k += TEAM) {
-      float z[NX];
-      btmv_row<NX>(Pd, Po, Rf, k, K, KP, z);
+      dfl z[NX];
+      btmv_row_df<NX>(Pd, Po, R, k, K, KP, z);
 #pragma unroll
-      for (int i = 0; i < NX; ++i) { Y[i * KP + k] = (double)z[i]; e1[0] += Rv[i * KP + k] * (double)z[i]; }
+      for (int i = 0; i < NX; ++i) { Y[i * KP + k] = z[i]; dacc_fma(na, R[i * KP + k], z[i]); }
     }
-    c.tm.sum(e1);
+    const dfl eta_new = team_df_sum<TEAM>(c.tm, dacc_get(na));
     ++it;
-    const double beta = e1[0] / eta;
-    eta = e1[0];
-    if (!(eta > tol2 * eta0)) { converged = true; break; }
+    if (!(eta_new.hi > thr.hi)) { converged = true; break; }
+    if (!isfinite(eta_new.hi)) break;
+    const dfl beta = df_div(eta_new, eta);
+    eta = eta_new;
     for (int k = c.tm.lane; k < K; k += TEAM)
 #pragma unroll
-      for (int i = 0; i < NX; ++i) Pv[i * KP + k] = Y[i * KP + k] + beta * Pv[i * KP + k];
+      for (int i = 0; i < NX; ++i) Pv[i * KP + k] = df_add(Y[i * KP + k], df_mul(beta, Pv[i * KP + k]));
     c.tm.sync();
   }
-  hp_residual<M, TEAM>(c, LP);  // leaves w = H^T lambda for the recovery
+  for (int k = c.tm.lane; k < K; k += TEAM)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) LP[i * KP + k] = df_to(X[i * KP + k]);
+  hp_residual<M, TEAM>(c, LP);  // leaves w = H^T lambda (FP64) for the recovery
   if (!converged) c.status |= ST_PCG_MAXITER;
   return it;
 }
@@ -1007,9 +1115,9 @@ __device__ __noinline__ int stage_pcg(Ctx<M, TEAM>& c) {
     hp_residual<M, TEAM>(c, LP);
   }
   if (!converged) {
-    // per-OCP FP64 rescue of this solve, continuing from the folded solution
+    // per-OCP double-float rescue of this solve, continuing from the folded solution
     c.status |= ST_FP64_RESCUE;
-    it += stage_pcg64<M, TEAM>(c, (double)eta0, maxit);
+    it += stage_pcg_df<M, TEAM>(c, eta0, maxit);
   }
   return it;
 }
@@ -1073,7 +1181,7 @@ __device__ __forceinline__ void reg_row(const float (&Md)[NX * NX], const float 
 }
 
 // a4, register-resident variant (one knot per lane, K <= TEAM, nx <= 4): the same algorithm
-// as stage_pcg (FP32 iteration, FP64 solution with reliable updates, FP64 rescue), with the
+// as stage_pcg (FP32 iteration, FP64 solution with reliable updates, double-float rescue), with the
 // S and Phi^-1 blocks of the lane's knot held in registers for the whole solve and the
 // neighbour coupling done with shuffles, so the inner loop touches no memory.
 template <class M, int TEAM>
@@ -1208,7 +1316,7 @@ __device__ __noinline__ int stage_pcg_reg(Ctx<M, TEAM>& c) {
   c.tm.buf = tm.buf;
   if (!converged) {
     c.status |= ST_FP64_RESCUE;
-    it += stage_pcg64<M, TEAM>(c, (double)eta0, maxit);
+    it += stage_pcg_df<M, TEAM>(c, eta0, maxit);
   }
   return it;
 }
@@ -1278,10 +1386,10 @@ __device__ __forceinline__ void warp_btmv_df(const float (&Md)[KPL][NX * NX], co
   for (int j = 0; j < KPL; ++j)
 #pragma unroll
     for (int b = 0; b < NX; ++b) {
-      dfl a = df_make(0.f);
+      dacc a = dacc_zero();
 #pragma unroll
-      for (int i = 0; i < NX; ++i) a = df_fmaf(a, Mo[j][i * NX + b], v[j][i]);
-      t[j][b] = a;
+      for (int i = 0; i < NX; ++i) dacc_fma(a, Mo[j][i * NX + b], v[j][i]);
+      t[j][b] = dacc_get(a);
     }
   dfl vm[NX], tn[NX];
 #pragma unroll
@@ -1297,13 +1405,14 @@ __device__ __forceinline__ void warp_btmv_df(const float (&Md)[KPL][NX * NX], co
   for (int j = 0; j < KPL; ++j)
 #pragma unroll
     for (int i = 0; i < NX; ++i) {
-      dfl a = (j + 1 < KPL) ? t[j + 1 < KPL ? j + 1 : 0][i] : tn[i];
+      dacc a = dacc_zero();
+      dacc_add(a, (j + 1 < KPL) ? t[j + 1 < KPL ? j + 1 : 0][i] : tn[i]);
 #pragma unroll
       for (int q = 0; q < NX; ++q) {
-        a = df_fmaf(a, Mo[j][i * NX + q], (j > 0) ? v[j > 0 ? j - 1 : 0][q] : vm[q]);
-        a = df_fmaf(a, Md[j][i * NX + q], v[j][q]);
+        dacc_fma(a, Mo[j][i * NX + q], (j > 0) ? v[j > 0 ? j - 1 : 0][q] : vm[q]);
+        dacc_fma(a, Md[j][i * NX + q], v[j][q]);
       }
-      out[j][i] = a;
+      out[j][i] = dacc_get(a);
     }
 }
 
@@ -1318,17 +1427,17 @@ __device__ __forceinline__ void warp_S_df(const float (&Ak)[KPL][M::NX * M::NX],
   for (int j = 0; j < KPL; ++j) {
 #pragma unroll
     for (int b = 0; b < NX; ++b) {
-      dfl a = df_make(0.f);
+      dacc a = dacc_zero();
 #pragma unroll
-      for (int i = 0; i < NX; ++i) a = df_fmaf(a, Ak[j][i * NX + b], v[j][i]);
-      t[j][b] = a;
+      for (int i = 0; i < NX; ++i) dacc_fma(a, Ak[j][i * NX + b], v[j][i]);
+      t[j][b] = dacc_get(a);
     }
 #pragma unroll
     for (int b = 0; b < NU; ++b) {
-      dfl a = df_make(0.f);
+      dacc a = dacc_zero();
 #pragma unroll
-      for (int i = 0; i < NX; ++i) a = df_fmaf(a, Bk[j][i * NU + b], v[j][i]);
-      ub[j][b] = a;
+      for (int i = 0; i < NX; ++i) dacc_fma(a, Bk[j][i * NU + b], v[j][i]);
+      ub[j][b] = dacc_get(a);
     }
   }
   dfl tn[NX], ubn[NU];
@@ -1371,12 +1480,13 @@ __device__ __forceinline__ void warp_S_df(const float (&Ak)[KPL][M::NX * M::NX],
   for (int j = 0; j < KPL; ++j)
 #pragma unroll
     for (int i = 0; i < NX; ++i) {
-      dfl a = vx[j][i];
+      dacc a = dacc_zero();
+      dacc_add(a, vx[j][i]);
 #pragma unroll
-      for (int q = 0; q < NX; ++q) a = df_fmaf(a, Ak[j][i * NX + q], (j > 0) ? vx[j > 0 ? j - 1 : 0][q] : vxm[q]);
+      for (int q = 0; q < NX; ++q) dacc_fma(a, Ak[j][i * NX + q], (j > 0) ? vx[j > 0 ? j - 1 : 0][q] : vxm[q]);
 #pragma unroll
-      for (int q = 0; q < NU; ++q) a = df_fmaf(a, Bk[j][i * NU + q], (j > 0) ? vu[j > 0 ? j - 1 : 0][q] : vum[q]);
-      out[j][i] = a;
+      for (int q = 0; q < NU; ++q) dacc_fma(a, Bk[j][i * NU + q], (j > 0) ? vu[j > 0 ? j - 1 : 0][q] : vum[q]);
+      out[j][i] = dacc_get(a);
     }
 }
 
@@ -1431,22 +1541,22 @@ __device__ __noinline__ int stage_pcg_warp_df(Ctx<M, 32>& c, float eta0f, int ma
 #pragma unroll
     for (int i = 0; i < NX; ++i) r[j][i] = live[j] ? df_sub(df_from(G[i * KP + ln * KPL + j]), y[j][i]) : df_make(0.f);
   warp_btmv_df<NX, KPL>(Pdk, Pok, r, z, ln);
-  dfl eta = df_make(0.f);
+  dacc ea = dacc_zero();
 #pragma unroll
   for (int j = 0; j < KPL; ++j)
 #pragma unroll
-    for (int i = 0; i < NX; ++i) { p[j][i] = z[j][i]; eta = df_add(eta, df_mul(r[j][i], z[j][i])); }
-  eta = df_warp_sum(eta);
+    for (int i = 0; i < NX; ++i) { p[j][i] = z[j][i]; dacc_fma(ea, r[j][i], z[j][i]); }
+  dfl eta = df_warp_sum(dacc_get(ea));
   int it = 0;
   bool converged = !(eta.hi > thr.hi);
   while (!converged && it < maxit) {
     warp_S_df<M, KPL>(Ak, Bk, qi, ri, has_u, p, y, ln);
-    dfl v = df_make(0.f);
+    dacc va = dacc_zero();
 #pragma unroll
     for (int j = 0; j < KPL; ++j)
 #pragma unroll
-      for (int i = 0; i < NX; ++i) v = df_add(v, df_mul(p[j][i], y[j][i]));
-    v = df_warp_sum(v);
+      for (int i = 0; i < NX; ++i) dacc_fma(va, p[j][i], y[j][i]);
+    const dfl v = df_warp_sum(dacc_get(va));
     if (!(v.hi > 0.f) || !isfinite(v.hi)) { c.status |= ST_PCG_BREAKDOWN; break; }
     const dfl alpha = df_div(eta, v);
 #pragma unroll
@@ -1457,12 +1567,12 @@ __device__ __noinline__ int stage_pcg_warp_df(Ctx<M, 32>& c, float eta0f, int ma
         r[j][i] = df_sub(r[j][i], df_mul(alpha, y[j][i]));
       }
     warp_btmv_df<NX, KPL>(Pdk, Pok, r, z, ln);
-    dfl eta_new = df_make(0.f);
+    dacc na = dacc_zero();
 #pragma unroll
     for (int j = 0; j < KPL; ++j)
 #pragma unroll
-      for (int i = 0; i < NX; ++i) eta_new = df_add(eta_new, df_mul(r[j][i], z[j][i]));
-    eta_new = df_warp_sum(eta_new);
+      for (int i = 0; i < NX; ++i) dacc_fma(na, r[j][i], z[j][i]);
+    const dfl eta_new = df_warp_sum(dacc_get(na));
     ++it;
     if (!(eta_new.hi > thr.hi)) { converged = true; break; }
     if (!isfinite(eta_new.hi)) break;
@@ -1485,7 +1595,7 @@ __device__ __noinline__ int stage_pcg_warp_df(Ctx<M, 32>& c, float eta0f, int ma
 
 // a4, single-warp variant (TEAM = 32, KPL contiguous knots per lane, K <= 32 KPL, nx <= 4):
 // the same algorithm as stage_pcg (Algorithm 4 in FP32 with FP64 reliable updates and the
-// FP64 rescue), with the S and Phi^-1 blocks of the lane's knots in registers for the whole
+// double-float rescue), with the S and Phi^-1 blocks of the lane's knots in registers for the whole
 // solve and every neighbour exchange and reduction done with warp shuffles: no shared memory
 // and no barrier inside the iteration.
 template <class M, int KPL>

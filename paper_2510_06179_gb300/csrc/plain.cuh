@@ -199,7 +199,7 @@ __device__ __noinline__ void plain_step(Ctx<M, TEAM>& c, PlainState& S, int step
       }
       if (!S.converged) {
         c.status |= ST_FP64_RESCUE;
-        it += stage_pcg64<M, TEAM>(c, (double)S.eta0, P.opt.pcg_max_iters);
+        it += stage_pcg_df<M, TEAM>(c, S.eta0, P.opt.pcg_max_iters);
       }
       if (c.tm.lane == 0) {
         S.it = it;

@@ -51,10 +51,10 @@ class Request:
 
 
 class SlotClass:
-    def __init__(self, model, nx, nu, t_lo, t_hi, dt, slots, options, device):
+    def __init__(self, model, nx, nu, t_lo, t_hi, dt, slots, options, device, priority=0):
         self.model, self.nx, self.nu, self.t_hi = model, nx, nu, t_hi
         self.batch = OCPBatch((model, nx, nu, t_hi, dt), batch=slots, device=device, **options)
-        self.stream = torch.cuda.Stream(device)
+        self.stream = torch.cuda.Stream(device, priority=priority)
         self.batch.stream = self.stream
         self.lib = self.batch.lib
         _lib.check(self.lib.dmpc_set_stream(self.batch.h, ctypes.c_void_p(self.stream.cuda_stream)), self.batch.h)
@@ -163,9 +163,13 @@ class ServingEngine:
         opts.update(options)
         self.classes = {}
         used = 0
+        # cheaper classes (smaller nx^2 T) get higher stream priority, so their blocks are
+        # scheduled first whenever heavier classes' blocks leave room on an SM
+        costs = sorted({nx * nx * hi for _, nx, _, _ in shapes for _, hi in T_BUCKETS})
         for model, nx, nu, dt in shapes:
             for lo, hi in T_BUCKETS:
-                c = SlotClass(model, nx, nu, lo, hi, dt, slots_per_class, opts, self.device)
+                prio = -(len(costs) - 1 - costs.index(nx * nx * hi))   # torch clamps to the device range
+                c = SlotClass(model, nx, nu, lo, hi, dt, slots_per_class, opts, self.device, prio)
                 c.batch.sqp_iters_total = sqp_iters
                 used += int(self.lib_bytes(c))
                 self.classes[(model, lo, hi)] = c
