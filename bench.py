@@ -460,6 +460,18 @@ def suite(path):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32).reshape(-1)).to(dev)
     out = {"device": torch.cuda.get_device_name(dev)}
 
+    # LQ (App. B.1): 16 OCPs, nx 4, nu 1, T 20, one SQP step with alpha = 1, forward only,
+    # tolerance 1e-8 (the one configuration with an exact closed form)
+    w = workloads.lq_config()
+    b = OCPBatch(("lq", 4, 1, w.T, 1.0), batch=w.B, device=dev, sqp_iters=1, line_search=0, pcg_tol=1e-8,
+                 warm_start=0)
+    inp = (t(w.x_s), t(w.theta), t(w.x_ref))
+    tf, _ = _timed(lambda: b.solve(*inp, want_stats=False), 50)
+    tp, tp_wall = _timed(lambda: b.solve(*inp, want_stats=False, plain=True), 10)
+    out["lq_b16"] = {"fused_fwd_ms": tf * 1e3, "plain_fwd_ms": max(tp, tp_wall) * 1e3,
+                     "speedup": max(tp, tp_wall) / tf}
+    b.close()
+
     # cart-pole batch (the headline workload): fused vs plain
     w = workload(0)
     b = OCPBatch(("cartpole", 4, 1, T, 0.05), batch=B, device=dev, sqp_iters=SQP_ITERS, line_search=1,

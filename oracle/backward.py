@@ -15,12 +15,17 @@ dl/dx_s = lambda~_0, because dg_0/dx_s = -I.
 import numpy as np
 
 from .ocp import (linearise, solve_qp, split_z, join_z, split_theta, theta_offsets,
-                  dynamics_jet, x_index, u_index)
+                  dynamics_jet, constraint_jet, x_index, u_index)
 
 
 def _phi_jets(ocp, z):
+    """Explicit integrators: Phi_t as Jets over (x_t, u_t, theta); implicit ones: f_t over
+    (x_t, u_t, x_{t+1}, theta).  Returns (g, h) first and second derivative arrays."""
     x, u = split_z(ocp, z)
-    jets, k = dynamics_jet(ocp, x[:, :-1], u, with_theta=True)
+    if ocp.model.implicit:
+        jets, k = constraint_jet(ocp, x, u, with_theta=True)
+    else:
+        jets, k = dynamics_jet(ocp, x[:, :-1], u, with_theta=True)
     g = np.stack([j.g for j in jets], axis=-2)    # (B, T, nx, k)
     h = np.stack([j.h for j in jets], axis=-3)    # (B, T, nx, k, k)
     return g, h
@@ -42,8 +47,19 @@ def dF_dtheta(ocp, z, lam, b, g=None, h=None):
     x, u = x[0], u[0]
     L = lam[b].reshape(T + 1, nx)
     M = np.zeros((n + m, p))
+    if ocp.model.implicit:
+        # f_t(x_t, u_t, x_{t+1}; theta): F_z rows of (x_t, u_t, x_{t+1}) get
+        # (d^2 f_t / dz dtheta)^T lambda_{t+1}; the F_lambda row block of f_t gets df_t/dtheta
+        zs = slice(0, 2 * nx + nu)
+        for t in range(T):
+            cols = np.concatenate([o_sh + np.arange(ps), o_kn + t * pk + np.arange(pk)]).astype(int)
+            th = slice(2 * nx + nu, 2 * nx + nu + ps + pk)
+            mixed = np.einsum("i,izj->zj", L[t + 1], h[bb, t][:, zs, th])
+            rows = np.concatenate([x_index(nx, nu, t), u_index(nx, nu, t), x_index(nx, nu, t + 1)])
+            M[np.ix_(rows, cols)] += mixed
+            M[np.ix_(n + (t + 1) * nx + np.arange(nx), cols)] += g[bb, t][:, th]
     zs = slice(0, nx + nu)                 # seeds of (x_t, u_t)
-    for t in range(T):
+    for t in range(T if not ocp.model.implicit else 0):
         cols = np.concatenate([o_sh + np.arange(ps), o_kn + t * pk + np.arange(pk)]).astype(int)
         th = slice(nx + nu, nx + nu + ps + pk)
         # F_z rows of (x_t, u_t): -(d^2 Phi_t / d(x,u) dtheta)^T lambda_{t+1}
@@ -65,6 +81,8 @@ def exact_hessian_blocks(ocp, z, lam, b, h=None):
     """Per-stage blocks of grad^2_zz L over (x_t, u_t): diag(Q, R) + sum_i lambda_{t+1,i} grad^2 f_{t,i}
     with f_t = x_{t+1} - Phi_t, so grad^2 f_t = -grad^2 Phi_t.  True (unprojected) weights."""
     nx, nu, T = ocp.nx, ocp.nu, ocp.T
+    if ocp.model.implicit:
+        raise NotImplementedError("implicit integrators couple knots in the Lagrangian Hessian")
     _, _, qd, rd, qtd = split_theta(ocp.one(b))
     if h is None:
         _, h = _phi_jets(ocp.one(b), z[b:b + 1])

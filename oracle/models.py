@@ -2,10 +2,12 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-Every model here is explicit: the constraint is f_t(x_{t+1}, x_t, u_t) = x_{t+1} - Phi_t(x_t, u_t)
+By default a model is explicit: the constraint is f_t(x_{t+1}, x_t, u_t) = x_{t+1} - Phi_t(x_t, u_t)
 with Phi_t a one-step integrator of continuous dynamics (RK4 or forward Euler), or the
 affine map of the LQ benchmark (App. B.1, "QP problems").  Hence A_t^+ = I,
-A_t = -dPhi/dx, B_t = -dPhi/du in Eq. 4.
+A_t = -dPhi/dx, B_t = -dPhi/du in Eq. 4.  A continuous model can instead use the implicit
+trapezoidal rule (integrator "trapezoid"): f_t = x_{t+1} - x_t - dt/2 (F(x_t, u_t) + F(x_{t+1}, u_t)),
+which makes A_t^+ = I - dt/2 dF/dx(x_{t+1}, u_t) a general matrix (the A^+ of Eq. 4 and 10).
 
 Parameters theta of a model are split into `p_shared` entries common to all knots and
 `p_knot` entries that belong to one knot t (only the LQ model has those: its A_t, B_t, c_t).
@@ -50,9 +52,22 @@ class Model:
         raise NotImplementedError
 
     def step(self, x, u, ths, thk):
-        """Phi_t(x_t, u_t; theta): the discrete one-step map."""
+        """Phi_t(x_t, u_t; theta): the discrete one-step map (explicit integrators)."""
         integ = rk4 if self.integrator == "rk4" else euler
         return integ(self.fc, x, u, ths, self.dt)
+
+    @property
+    def implicit(self):
+        return self.integrator == "trapezoid"
+
+    def residual(self, x, u, xn, ths, thk):
+        """f_t(x_t, u_t, x_{t+1}; theta), the dynamics constraint written implicitly."""
+        if self.implicit:
+            fa = self.fc(x, u, ths)
+            fb = self.fc(xn, u, ths)
+            return [xn[i] - x[i] - (0.5 * self.dt) * (fa[i] + fb[i]) for i in range(self.nx)]
+        phi = self.step(x, u, ths, thk)
+        return [xn[i] - phi[i] for i in range(self.nx)]
 
 
 class LQ(Model):
@@ -239,9 +254,13 @@ class Attitude(Model):
         return [(c1 + u[0]) / j1, (c2 + u[1]) / j2, (c3 + u[2]) / j3]
 
 
-def make_model(name, nx=None, nu=None, dt=0.05):
+def make_model(name, nx=None, nu=None, dt=0.05, integrator=None):
+    """integrator: None (the model's own) or "trapezoid" (implicit trapezoidal rule)."""
     if name == "lq":
         return LQ(nx, nu)
     table = {"pendulum": Pendulum, "cartpole": CartPole, "kin_bicycle": KinematicBicycle,
              "single_track": SingleTrackFiala, "rigid_body12": RigidBody12, "attitude": Attitude}
-    return table[name](dt)
+    m = table[name](dt)
+    if integrator is not None:
+        m.integrator = integrator
+    return m

@@ -122,11 +122,22 @@ def dynamics_values(ocp, x, u, t0=0):
 
 
 def constraint_residual(ocp, z):
-    """g(z) = (x_0 - x_s, f_0, ..., f_{T-1}), f_t = x_{t+1} - Phi_t(x_t, u_t).  (B, T+1, nx)."""
+    """g(z) = (x_0 - x_s, f_0, ..., f_{T-1}), f_t = x_{t+1} - Phi_t(x_t, u_t) (or the implicit
+    trapezoidal residual).  (B, T+1, nx)."""
     x, u = split_z(ocp, z)
-    phi = dynamics_values(ocp, x[:, :-1], u)
     g = np.empty_like(x)
     g[:, 0] = x[:, 0] - ocp.x_s
+    if ocp.model.implicit:
+        ths, thk, _, _, _ = split_theta(ocp)
+        mdl = ocp.model
+        xs = [x[:, :-1, i] for i in range(mdl.nx)]
+        xn = [x[:, 1:, i] for i in range(mdl.nx)]
+        us = [u[..., i] for i in range(mdl.nu)]
+        sh = [ths[:, None, i] for i in range(mdl.p_shared)]
+        out = mdl.residual(xs, us, xn, sh, [thk[..., i] for i in range(mdl.p_knot)])
+        g[:, 1:] = np.stack([np.broadcast_to(value(o), x[:, 1:].shape[:2]) for o in out], axis=-1)
+        return g
+    phi = dynamics_values(ocp, x[:, :-1], u)
     g[:, 1:] = x[:, 1:] - phi
     return g
 
@@ -151,6 +162,27 @@ def dynamics_jet(ocp, x, u, with_theta=False):
     out = mdl.step(xs, us, sh, kn)
     out = [o if isinstance(o, Jet) else Jet(np.broadcast_to(o, shape), np.zeros(shape + (k,)),
                                             np.zeros(shape + (k, k))) for o in out]
+    return out, k
+
+
+def constraint_jet(ocp, x, u, with_theta=False):
+    """f_t as Jets seeded on (x_t, u_t, x_{t+1}[, theta_shared, theta_knot_t]) for the implicit
+    integrators; x: (B, T+1, nx), u: (B, T, nu).  Returns (list of nx Jets over (B, T), k)."""
+    mdl = ocp.model
+    ths, thk, _, _, _ = split_theta(ocp)
+    nx, nu, ps, pk = mdl.nx, mdl.nu, mdl.p_shared, mdl.p_knot
+    k = 2 * nx + nu + ((ps + pk) if with_theta else 0)
+    shape = u.shape[:2]
+    xs = [Jet.seed(x[:, :-1, i], i, k) for i in range(nx)]
+    us = [Jet.seed(u[..., i], nx + i, k) for i in range(nu)]
+    xn = [Jet.seed(x[:, 1:, i], nx + nu + i, k) for i in range(nx)]
+    if with_theta:
+        sh = [Jet.seed(np.broadcast_to(ths[:, None, i], shape), 2 * nx + nu + i, k) for i in range(ps)]
+        kn = [Jet.seed(thk[..., i], 2 * nx + nu + ps + i, k) for i in range(pk)]
+    else:
+        sh = [ths[:, None, i] for i in range(ps)]
+        kn = [thk[..., i] for i in range(pk)]
+    out = mdl.residual(xs, us, xn, sh, kn)
     return out, k
 
 
@@ -203,13 +235,21 @@ def linearise(ocp, z):
     (so that the QP is posed in absolute z as in Sec. 3.1) and C_t from its definition."""
     x, u = split_z(ocp, z)
     nx, nu, T = ocp.nx, ocp.nu, ocp.T
-    jets, _ = dynamics_jet(ocp, x[:, :-1], u)
-    phi = np.stack([j.v for j in jets], axis=-1)               # (B, T, nx)
-    jac = np.stack([j.g for j in jets], axis=-2)               # (B, T, nx, nx+nu)
-    A = -jac[..., :nx]
-    Bm = -jac[..., nx:nx + nu]
-    Ap = np.broadcast_to(np.eye(nx), A.shape).copy()
-    f = x[:, 1:] - phi
+    if ocp.model.implicit:
+        jets, _ = constraint_jet(ocp, x, u)
+        f = np.stack([j.v for j in jets], axis=-1)             # (B, T, nx)
+        jac = np.stack([j.g for j in jets], axis=-2)           # (B, T, nx, 2nx+nu)
+        A = jac[..., :nx].copy()
+        Bm = jac[..., nx:nx + nu].copy()
+        Ap = jac[..., nx + nu:2 * nx + nu].copy()
+    else:
+        jets, _ = dynamics_jet(ocp, x[:, :-1], u)
+        phi = np.stack([j.v for j in jets], axis=-1)           # (B, T, nx)
+        jac = np.stack([j.g for j in jets], axis=-2)           # (B, T, nx, nx+nu)
+        A = -jac[..., :nx]
+        Bm = -jac[..., nx:nx + nu]
+        Ap = np.broadcast_to(np.eye(nx), A.shape).copy()
+        f = x[:, 1:] - phi
     C = (np.einsum("btij,btj->bti", Ap, x[:, 1:]) + np.einsum("btij,btj->bti", A, x[:, :-1])
          + np.einsum("btij,btj->bti", Bm, u) - f)
     Qd, Rd = cost_hessians(ocp)
@@ -330,11 +370,20 @@ def kkt_residual(ocp, z, lam):
     """F(z, lambda) of Eq. 1 for the OCP: (grad_z c + (dg/dz)^T lambda, g).  Returns (Fz, Fl)."""
     x, u = split_z(ocp, z)
     nx, nu, T = ocp.nx, ocp.nu, ocp.T
-    jets, _ = dynamics_jet(ocp, x[:, :-1], u)
-    jac = np.stack([j.g for j in jets], axis=-2)     # dPhi/d(x,u): (B, T, nx, nx+nu)
     L = lam.reshape(lam.shape[0], T + 1, nx)
     gz = cost_gradient(ocp, z)
     gx, gu = split_z(ocp, gz)
+    if ocp.model.implicit:
+        jets, _ = constraint_jet(ocp, x, u)
+        jac = np.stack([j.g for j in jets], axis=-2)  # df_t/d(x_t, u_t, x_{t+1})
+        gx = gx.copy()
+        gx[:, 0] += L[:, 0]
+        gx[:, :-1] += np.einsum("btij,bti->btj", jac[..., :nx], L[:, 1:])
+        gx[:, 1:] += np.einsum("btij,bti->btj", jac[..., nx + nu:], L[:, 1:])
+        gu = gu + np.einsum("btij,bti->btj", jac[..., nx:nx + nu], L[:, 1:])
+        return join_z(gx, gu), constraint_residual(ocp, z).reshape(z.shape[0], -1)
+    jets, _ = dynamics_jet(ocp, x[:, :-1], u)
+    jac = np.stack([j.g for j in jets], axis=-2)     # dPhi/d(x,u): (B, T, nx, nx+nu)
     # g_0 = x_0 - x_s contributes lambda_0 to x_0; f_t = x_{t+1} - Phi_t contributes
     # lambda_{t+1} to x_{t+1} and -(dPhi/dx)^T lambda_{t+1}, -(dPhi/du)^T lambda_{t+1}.
     gx = gx + L

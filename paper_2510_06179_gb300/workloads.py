@@ -55,6 +55,7 @@ class Workload:
     pcg_tol: float = 1e-8
     u_target: np.ndarray = None   # (B, nu) float32: loss l = ||u_0 - u_target||^2
     extra: dict = field(default_factory=dict)
+    integrator: str = None        # None: the model's own; "trapezoid": implicit trapezoidal rule
 
     @property
     def B(self):
@@ -192,7 +193,7 @@ def rl_lq_problem(problem=1, seed=0, B=None, H=None, T=None):
     return RLProblem(nx, nu, T, H, _f32(A), _f32(Bm), _f32(b), _f32(x0), _f32(q0))
 
 
-def cartpole_config(B=256, T=50, seed=0, sqp_iters=10, pcg_tol=1e-6, dt=0.05):
+def cartpole_config(B=256, T=50, seed=0, sqp_iters=10, pcg_tol=1e-6, dt=0.05, integrator=None):
     """Cart-pole swing-up/balance: m_p ~ U[0.05, 0.2], L ~ U[0.3, 0.7], diag Q ~ U[0.1, 10],
     diag R ~ U[0.01, 1], Q_T = 10 Q; x_0: angle ~ U[-pi, pi], other states ~ N(0, 0.5);
     reference = upright at rest; loss target u_target ~ N(0, 1)."""
@@ -204,12 +205,12 @@ def cartpole_config(B=256, T=50, seed=0, sqp_iters=10, pcg_tol=1e-6, dt=0.05):
     x_s[:, 2] = rng.uniform(-np.pi, np.pi, size=B)
     th = _pack_theta("cartpole", 4, 1, T, np.stack([mp, L], 1), None, q, r, qt)
     u_t = rng.standard_normal((B, 1))
-    return Workload("cartpole", "cartpole", 4, 1, T, dt, _f32(x_s), _f32(th),
-                    _f32(np.zeros((B, T + 1, 4))), sqp_iters=sqp_iters, line_search=True,
-                    pcg_tol=pcg_tol, u_target=_f32(u_t))
+    return Workload("cartpole" if integrator is None else f"cartpole_{integrator}", "cartpole", 4, 1, T, dt,
+                    _f32(x_s), _f32(th), _f32(np.zeros((B, T + 1, 4))), sqp_iters=sqp_iters, line_search=True,
+                    pcg_tol=pcg_tol, u_target=_f32(u_t), integrator=integrator)
 
 
-def pendulum_config(B=64, T=40, seed=0, sqp_iters=10, pcg_tol=1e-6, dt=0.05):
+def pendulum_config(B=64, T=40, seed=0, sqp_iters=10, pcg_tol=1e-6, dt=0.05, integrator=None):
     """Pendulum swing-up/balance: m ~ U[0.5, 2], L ~ U[0.5, 1.5]; angle ~ U[-pi, pi], rate ~ N(0, 0.5)."""
     rng = np.random.default_rng(seed)
     m = rng.uniform(0.5, 2.0, size=B)
@@ -217,9 +218,9 @@ def pendulum_config(B=64, T=40, seed=0, sqp_iters=10, pcg_tol=1e-6, dt=0.05):
     q, r, qt = _cost_weights(rng, B, 2, 1)
     x_s = np.stack([rng.uniform(-np.pi, np.pi, size=B), np.sqrt(0.5) * rng.standard_normal(B)], 1)
     th = _pack_theta("pendulum", 2, 1, T, np.stack([m, L], 1), None, q, r, qt)
-    return Workload("pendulum", "pendulum", 2, 1, T, dt, _f32(x_s), _f32(th),
-                    _f32(np.zeros((B, T + 1, 2))), sqp_iters=sqp_iters, line_search=True,
-                    pcg_tol=pcg_tol, u_target=_f32(rng.standard_normal((B, 1))))
+    return Workload("pendulum" if integrator is None else f"pendulum_{integrator}", "pendulum", 2, 1, T, dt,
+                    _f32(x_s), _f32(th), _f32(np.zeros((B, T + 1, 2))), sqp_iters=sqp_iters, line_search=True,
+                    pcg_tol=pcg_tol, u_target=_f32(rng.standard_normal((B, 1))), integrator=integrator)
 
 
 def bicycle_config(B=64, T=40, seed=0, sqp_iters=10, pcg_tol=1e-6, dt=0.05):

@@ -10,7 +10,7 @@ def to_ocp(w, idx=None):
     x_s, th, xr = w.x_s, w.theta, w.x_ref
     if idx is not None:
         x_s, th, xr = x_s[idx], th[idx], xr[idx]
-    model = make_model(w.model, w.nx, w.nu, w.dt)
+    model = make_model(w.model, w.nx, w.nu, w.dt, integrator=getattr(w, "integrator", None))
     return OCPBatch(model, w.T, x_s.astype(np.float64), th.astype(np.float64), xr.astype(np.float64))
 
 
