@@ -483,6 +483,17 @@ def suite(path):
     out["cartpole_b256"] = _fused_vs_plain(b, inp, dl, 5, B)
     b.close()
 
+    # the same cart-pole batch with the implicit trapezoidal rule (A^+ != I)
+    w = workloads.cartpole_config(B=B, T=T, seed=1000, sqp_iters=SQP_ITERS, integrator="trapezoid")
+    b = OCPBatch(("cartpole", 4, 1, T, 0.05, "trapezoid"), batch=B, device=dev, sqp_iters=SQP_ITERS,
+                 line_search=1, pcg_tol=PCG_TOL, warm_start=0)
+    inp = (t(w.x_s), t(w.theta), t(w.x_ref))
+    z = b.solve(*inp)["z"]
+    dl = torch.zeros_like(z)
+    dl.view(B, -1)[:, 4] = 1.0
+    out["cartpole_trapezoid_b256"] = _fused_vs_plain(b, inp, dl, 5, B)
+    b.close()
+
     # uneven batch: 4096 OCPs of three models, T ~ U{16..128}, one persistent launch,
     # autotuned tiling, CUDA-graph replay
     items = workloads.uneven_mix(n_ocps=4096, seed=0, sqp_iters=SQP_ITERS, pcg_tol=PCG_TOL)

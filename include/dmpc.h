@@ -79,12 +79,21 @@ typedef enum {
   DMPC_MODEL_ATTITUDE = 6
 } dmpc_model;
 
+/* Integrator of a continuous model (dmpc_ocp_desc.integrator). */
+typedef enum {
+  DMPC_INTEGRATOR_DEFAULT = 0,   /* the model's explicit step (RK4; Euler for attitude; affine LQ) */
+  DMPC_INTEGRATOR_TRAPEZOID = 1  /* implicit trapezoidal rule f_t = x_{t+1} - x_t - dt/2 (F(x_t, u_t)
+                                    + F(x_{t+1}, u_t)), so A^+ = I - dt/2 dF/dx (Eq. 4, 10);
+                                    pendulum and cart-pole; not with exact_hessian */
+} dmpc_integrator;
+
 /* One OCP of a batch (the OCP statement of Sec. 3): model, sizes, horizon, step. */
 typedef struct {
-  int model;   /* dmpc_model */
-  int nx, nu;  /* state / input dimension (must match the model) */
-  int T;       /* horizon, 1 <= T <= 4096 */
-  float dt;    /* integrator step (ignored by LQ) */
+  int model;      /* dmpc_model */
+  int nx, nu;     /* state / input dimension (must match the model) */
+  int T;          /* horizon, 1 <= T <= 4096 */
+  float dt;       /* integrator step (ignored by LQ) */
+  int integrator; /* dmpc_integrator; 0 = the model's own */
 } dmpc_ocp_desc;
 
 /* Solver options.  dmpc_default_options() fills the defaults noted here. */

@@ -14,7 +14,8 @@ P = c_void_p
 
 
 class dmpc_ocp_desc(ctypes.Structure):
-    _fields_ = [("model", c_int), ("nx", c_int), ("nu", c_int), ("T", c_int), ("dt", c_float)]
+    _fields_ = [("model", c_int), ("nx", c_int), ("nu", c_int), ("T", c_int), ("dt", c_float),
+                ("integrator", c_int)]
 
 
 class dmpc_options(ctypes.Structure):

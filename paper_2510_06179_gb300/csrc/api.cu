@@ -59,6 +59,17 @@ bool model_info(int model, int nx, int nu, ModelInfo* mi) {
 
 int p_knot(int model, int nx, int nu) { return model == DMPC_MODEL_LQ ? nx * nx + nx * nu + nx : 0; }
 
+// Kernel-side model id: the trapezoidal (implicit) variants have their own instantiations.
+// Returns -1 for an integrator the model does not support.
+int kernel_model_id(const dmpc_ocp_desc& d) {
+  if (d.integrator == DMPC_INTEGRATOR_DEFAULT) return d.model;
+  if (d.integrator == DMPC_INTEGRATOR_TRAPEZOID &&
+      (d.model == DMPC_MODEL_PENDULUM || d.model == DMPC_MODEL_CARTPOLE))
+    return d.model + kTrapIdOffset;
+  return -1;
+}
+int is_implicit_desc(const dmpc_ocp_desc& d) { return d.integrator == DMPC_INTEGRATOR_TRAPEZOID ? 1 : 0; }
+
 std::mutex g_reg_mu;
 std::vector<KernelEntry> g_registry;
 std::string g_create_error;
@@ -208,7 +219,7 @@ static dmpc_err configure_tiling(dmpc_handle* h, int team, int tpb) {
     else team = maxK <= 48 ? 32 : (maxK <= 160 ? 64 : (maxK <= 320 ? 128 : 256));
   }
   int ws = 0;
-  for (auto& d : h->descs) ws = std::max(ws, make_layout(d.nx, d.nu, d.T + 1, team, h->opt.exact_hessian).total_floats);
+  for (auto& d : h->descs) ws = std::max(ws, make_layout(d.nx, d.nu, d.T + 1, team, h->opt.exact_hessian, is_implicit_desc(d)).total_floats);
   const size_t ws_bytes = (size_t)ws * sizeof(float);
   const int max_tpb_threads = 256 / team;
   h->use_gws = ws_bytes > (size_t)h->smem_optin;
@@ -227,9 +238,11 @@ static dmpc_err configure_tiling(dmpc_handle* h, int team, int tpb) {
     if (h->uniform && e.model == h->model0 && e.nx == h->nx0 && e.nu == h->nu0) { fn = e.fn; pfn = e.plain; break; }
   }
   if (!fn) {
-    bool has_lq = false;
-    for (auto& d : h->descs) has_lq |= d.model == DMPC_MODEL_LQ;
+    bool has_lq = false, has_implicit = false;
+    for (auto& d : h->descs) { has_lq |= d.model == DMPC_MODEL_LQ; has_implicit |= is_implicit_desc(d) != 0; }
     if (has_lq) return fail(h, DMPC_E_UNSUPPORTED, "LQ OCPs cannot be mixed with other models in one batch");
+    if (has_implicit)
+      return fail(h, DMPC_E_UNSUPPORTED, "implicit-integrator OCPs cannot be mixed with other models in one batch");
     for (auto& e : registry())
       if (e.model == -1 && e.team == team) { fn = e.fn; pfn = e.plain; break; }
   }
@@ -272,7 +285,7 @@ extern "C" dmpc_err dmpc_create_problem_batch(const dmpc_ocp_desc* descs, int ba
   if (ce != cudaSuccess) { delete h; return cuda_fail(nullptr, ce, "cudaGetDevice"); }
   cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
   cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-  h->model0 = descs[0].model; h->nx0 = descs[0].nx; h->nu0 = descs[0].nu;
+  h->model0 = kernel_model_id(descs[0]); h->nx0 = descs[0].nx; h->nu0 = descs[0].nu;
   h->recs.resize(batch);
   h->rec_off.resize(batch + 1);
   std::vector<double> cost(batch);
@@ -284,14 +297,22 @@ extern "C" dmpc_err dmpc_create_problem_batch(const dmpc_ocp_desc* descs, int ba
       return fail(nullptr, DMPC_E_UNSUPPORTED, "OCP " + std::to_string(b) + ": unknown model or sizes not matching the model");
     }
     if (d.T < 1 || d.T > 4096) { delete h; return fail(nullptr, DMPC_E_ARG, "OCP " + std::to_string(b) + ": T must be in [1, 4096]"); }
+    if (kernel_model_id(d) < 0) {
+      delete h;
+      return fail(nullptr, DMPC_E_UNSUPPORTED, "OCP " + std::to_string(b) + ": integrator not available for this model");
+    }
+    if (is_implicit_desc(d) && h->opt.exact_hessian) {
+      delete h;
+      return fail(nullptr, DMPC_E_UNSUPPORTED, "exact_hessian is not available with implicit integrators");
+    }
     if (d.model != DMPC_MODEL_LQ && !(d.dt > 0.f && std::isfinite(d.dt))) {
       delete h;
       return fail(nullptr, DMPC_E_ARG, "OCP " + std::to_string(b) + ": dt must be positive");
     }
-    h->uniform &= (d.model == h->model0 && d.nx == h->nx0 && d.nu == h->nu0);
+    h->uniform &= (kernel_model_id(d) == h->model0 && d.nx == h->nx0 && d.nu == h->nu0);
     const int K = d.T + 1;
     OcpRec& r = h->recs[b];
-    r.model = d.model; r.nx = d.nx; r.nu = d.nu; r.T = d.T; r.dt = d.dt;
+    r.model = kernel_model_id(d); r.nx = d.nx; r.nu = d.nu; r.T = d.T; r.dt = d.dt;
     r.n = K * d.nx + d.T * d.nu;
     r.m = K * d.nx;
     r.p = mi.p_shared + d.T * p_knot(d.model, d.nx, d.nu) + 2 * d.nx + d.nu;
@@ -509,7 +530,7 @@ static const int kPlainPoll = 8;
 static dmpc_err plain_prepare(dmpc_handle* h, KParams* P) {
   const int team = h->team;
   int ws = 0;
-  for (auto& d : h->descs) ws = std::max(ws, make_layout(d.nx, d.nu, d.T + 1, team, h->opt.exact_hessian).total_floats);
+  for (auto& d : h->descs) ws = std::max(ws, make_layout(d.nx, d.nu, d.T + 1, team, h->opt.exact_hessian, is_implicit_desc(d)).total_floats);
   if (!h->plain_ws || ws != h->plain_ws_floats) {
     cudaFree(h->plain_ws);
     h->plain_ws = nullptr;
@@ -657,20 +678,23 @@ extern "C" dmpc_err dmpc_set_ocps(dmpc_handle* h, int n, const int* index, const
     if (b < 0 || b >= h->batch) return fail(h, DMPC_E_ARG, "slot index out of range");
     const dmpc_ocp_desc& d = descs[i];
     ModelInfo mi;
-    if (!model_info(d.model, d.nx, d.nu, &mi) || d.T < 1) return fail(h, DMPC_E_UNSUPPORTED, "bad slot shape");
-    if (h->uniform && (d.model != h->model0 || d.nx != h->nx0 || d.nu != h->nu0))
+    if (!model_info(d.model, d.nx, d.nu, &mi) || d.T < 1 || kernel_model_id(d) < 0)
+      return fail(h, DMPC_E_UNSUPPORTED, "bad slot shape");
+    if (h->uniform && (kernel_model_id(d) != h->model0 || d.nx != h->nx0 || d.nu != h->nu0))
       return fail(h, DMPC_E_UNSUPPORTED, "a single-model handle cannot take another model");
+    if (is_implicit_desc(d) && h->opt.exact_hessian)
+      return fail(h, DMPC_E_UNSUPPORTED, "exact_hessian is not available with implicit integrators");
     if (d.model != DMPC_MODEL_LQ && !(d.dt > 0.f)) return fail(h, DMPC_E_ARG, "dt must be positive");
     const OcpRec& c = h->cap[b];
     OcpRec r = c;
     const int K = d.T + 1;
-    r.model = d.model; r.nx = d.nx; r.nu = d.nu; r.T = d.T; r.dt = d.dt;
+    r.model = kernel_model_id(d); r.nx = d.nx; r.nu = d.nu; r.T = d.T; r.dt = d.dt;
     r.n = K * d.nx + d.T * d.nu;
     r.m = K * d.nx;
     r.p = mi.p_shared + d.T * p_knot(d.model, d.nx, d.nu) + 2 * d.nx + d.nu;
     if (r.n > c.n || r.m > c.m || r.p > c.p || d.nx > c.nx || (long long)K * d.nx > (long long)(c.T + 1) * c.nx ||
         (long long)K * (5 * d.nx * d.nx + d.nx * d.nu) > (long long)(c.T + 1) * (5 * c.nx * c.nx + c.nx * c.nu) ||
-        make_layout(d.nx, d.nu, K, h->team, h->opt.exact_hessian).total_floats > h->max_ws_floats)
+        make_layout(d.nx, d.nu, K, h->team, h->opt.exact_hessian, is_implicit_desc(d)).total_floats > h->max_ws_floats)
       return fail(h, DMPC_E_BUDGET, "shape exceeds the slot's capacity");
     h->recs[b] = r;
     upd[i] = r;

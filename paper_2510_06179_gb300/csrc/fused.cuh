@@ -37,13 +37,14 @@ constexpr int kRedMax = 48;     // must equal Team<>::RED_MAX
 struct Layout {
   int KP;
   int d_lam, d_lamp, d_gam, d_wx, d_wu, d_r, d_p, d_y, d_W, d_total;  // double arrays (in doubles)
-  int x, u, xp, up, f, C, A, Bm, D, O, Pd, Po, r, p, y, dl, misc, red, bnd, f_total;  // floats
+  int x, u, xp, up, f, C, A, Bm, Ap, D, O, Pd, Po, r, p, y, dl, misc, red, bnd, f_total;  // floats
   int total_floats;
 };
 
 // exact = 1 adds the exact-Hessian backward's per-knot blocks ((nx+nu)^2 doubles per knot: the
-// Hessian block, then the Riccati factors) and its scratch.
-__host__ __device__ inline Layout make_layout(int nx, int nu, int K, int team, int exact = 0) {
+// Hessian block, then the Riccati factors) and its scratch; implicit = 1 adds the A^+ blocks of
+// an implicit integrator (nx^2 floats per knot).
+__host__ __device__ inline Layout make_layout(int nx, int nu, int K, int team, int exact = 0, int implicit = 0) {
   Layout L;
   L.KP = (K + 1) & ~1;
   const int KP = L.KP;
@@ -67,6 +68,7 @@ __host__ __device__ inline Layout make_layout(int nx, int nu, int K, int team, i
   L.C = f; f += nx * KP;
   L.A = f; f += nx * nx * KP;
   L.Bm = f; f += nx * nu * KP;
+  L.Ap = f; f += implicit ? nx * nx * KP : 0;
   L.D = f; f += nx * nx * KP;
   L.O = f; f += nx * nx * KP;
   L.Pd = f; f += nx * nx * KP;
@@ -354,6 +356,61 @@ __device__ __noinline__ void stage_linearise(Ctx<M, TEAM>& c) {
         phi[i] = acc;
         C[i * KP + k] = tk[NX * NX + NX * NU + i];
       }
+    } else if constexpr (is_implicit<M>::value) {
+      // trapezoidal rule: f = x_{t+1} - x_t - dt/2 (F(x_t, u_t) + F(x_{t+1}, u_t)), so
+      // A = -I - dt/2 F_x(x_t), B = -dt/2 (F_u(x_t) + F_u(x_{t+1})), A^+ = I - dt/2 F_x(x_{t+1})
+      float* Ap = c.F(c.L.Ap);
+      constexpr int CH = NZ <= 8 ? NZ : 8;
+      float pv[M::NP];
+#pragma unroll
+      for (int j = 0; j < M::NP; ++j) pv[j] = c.misc(MS_TH + j);
+      float xn[NX], fsum[NX], ja[NX * NZ], jb[NX * NZ];
+#pragma unroll
+      for (int i = 0; i < NX; ++i) xn[i] = X[i * KP + k];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const float* xe = side == 0 ? xt : xn;
+        float* jac = side == 0 ? ja : jb;
+#pragma unroll
+        for (int c0 = 0; c0 < NZ; c0 += CH) {
+          Dual<CH> xd[NX], ud[NU], pd[M::NP], out[NX];
+#pragma unroll
+          for (int i = 0; i < NX; ++i) xd[i] = Dual<CH>::seed(xe[i], i - c0);
+#pragma unroll
+          for (int i = 0; i < NU; ++i) ud[i] = Dual<CH>::seed(ut[i], NX + i - c0);
+#pragma unroll
+          for (int j = 0; j < M::NP; ++j) pd[j] = Dual<CH>(pv[j]);
+          M::f(xd, ud, pd, out);
+#pragma unroll
+          for (int i = 0; i < NX; ++i) {
+            if (c0 == 0) fsum[i] = (side == 0 ? 0.f : fsum[i]) + out[i].v;
+#pragma unroll
+            for (int q = 0; q < CH; ++q)
+              if (c0 + q < NZ) jac[i * NZ + c0 + q] = out[i].d[q];
+          }
+        }
+      }
+      const float h = 0.5f * c.dt;
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        phi[i] = xt[i] + h * fsum[i];  // so that f = x_{t+1} - phi below
+        float acc = 0.f;                // A^+ x_{t+1} + A x_t + B u_t
+#pragma unroll
+        for (int j = 0; j < NX; ++j) {
+          const float a = (i == j ? -1.f : 0.f) - h * ja[i * NZ + j];
+          const float ap = (i == j ? 1.f : 0.f) - h * jb[i * NZ + j];
+          A[(i * NX + j) * KP + k] = a;
+          Ap[(i * NX + j) * KP + k] = ap;
+          acc = fmaf(a, xt[j], fmaf(ap, xn[j], acc));
+        }
+#pragma unroll
+        for (int j = 0; j < NU; ++j) {
+          const float b = -h * (ja[i * NZ + NX + j] + jb[i * NZ + NX + j]);
+          Bm[(i * NU + j) * KP + k] = b;
+          acc = fmaf(b, ut[j], acc);
+        }
+        C[i * KP + k] = acc - (xn[i] - phi[i]);
+      }
     } else {
       constexpr int CH = NZ <= 8 ? NZ : 8;
       float pv[M::NP];
@@ -415,7 +472,7 @@ __device__ __noinline__ void stage_exact_hessian(Ctx<M, TEAM>& c) {
   const float* U = c.F(c.L.u);
   const double* LAM = c.Dp(c.L.d_lam);
   double* W = c.Dp(c.L.d_W);
-  if constexpr (!is_lq<M>::value)  // affine dynamics: no curvature (the exact mode is off for LQ)
+  if constexpr (!is_lq<M>::value && !is_implicit<M>::value)  // exact mode is off for these
   for (int k = c.tm.lane; k < T; k += TEAM) {
     float lam1[NX];
 #pragma unroll
@@ -631,6 +688,63 @@ __device__ __noinline__ void stage_schur(Ctx<M, TEAM>& c, bool rhs_from_qp) {
       continue;
     }
     const int t = k - 1;
+    if constexpr (is_implicit<M>::value) {
+      // general A^+ (Eq. 10): D_k = A Q_t^-1 A^T + B R^-1 B^T + A^+_k Q_k^-1 A^+_k^T,
+      // O_k = A_k Q_t^-1 (A^+_{k-1})^T (A^+_0 = I: row 0 is x_0 - x_s)
+      const float* Ap = c.F(c.L.Ap);
+      float qt[NX], ri[NU];
+#pragma unroll
+      for (int i = 0; i < NX; ++i) qt[i] = 1.f / c.qproj(t, i);
+#pragma unroll
+      for (int i = 0; i < NU; ++i) ri[i] = 1.f / c.misc(MS_RP + i);
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+          float sum = 0.f;
+#pragma unroll
+          for (int l = 0; l < NX; ++l) {
+            sum = fmaf(A[(i * NX + l) * KP + k] * qt[l], A[(j * NX + l) * KP + k], sum);
+            sum = fmaf(Ap[(i * NX + l) * KP + k] * qi[l], Ap[(j * NX + l) * KP + k], sum);
+          }
+#pragma unroll
+          for (int l = 0; l < NU; ++l) sum = fmaf(Bm[(i * NU + l) * KP + k] * ri[l], Bm[(j * NU + l) * KP + k], sum);
+          D[(i * NX + j) * KP + k] = sum;
+          D[(j * NX + i) * KP + k] = sum;
+        }
+#pragma unroll
+        for (int j = 0; j < NX; ++j) {
+          float sum = 0.f;
+#pragma unroll
+          for (int l = 0; l < NX; ++l) {
+            const float apv = (t == 0) ? (j == l ? 1.f : 0.f) : Ap[(j * NX + l) * KP + t];
+            sum = fmaf(A[(i * NX + l) * KP + k] * qt[l], apv, sum);
+          }
+          O[(i * NX + j) * KP + k] = sum;
+        }
+      }
+      if (rhs_from_qp) {
+        double vq[NX], vk[NX], vr[NU];
+#pragma unroll
+        for (int j = 0; j < NX; ++j) {
+          vq[j] = c.qlin(t, j, X[j * KP + t]) * c.qinv(t, j);
+          vk[j] = c.qlin(k, j, X[j * KP + k]) * c.qinv(k, j);
+        }
+#pragma unroll
+        for (int j = 0; j < NU; ++j) vr[j] = c.rlin(j, U[j * KP + t]) * c.rinv(j);
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+          double z = 0.0;
+#pragma unroll
+          for (int j = 0; j < NX; ++j)
+            z += (double)A[(i * NX + j) * KP + k] * vq[j] + (double)Ap[(i * NX + j) * KP + k] * vk[j];
+#pragma unroll
+          for (int j = 0; j < NU; ++j) z += (double)Bm[(i * NU + j) * KP + k] * vr[j];
+          G[i * KP + k] = -(double)C[i * KP + k] - z;
+        }
+      }
+      continue;
+    }
     float qt[NX], ri[NU];
 #pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = 0; i < NX; ++i) qt[i] = 1.f / c.qproj(t, i);
@@ -739,6 +853,21 @@ __device__ __noinline__ void hp_apply(Ctx<M, TEAM>& c, const double* src, bool r
     double wx[NX];
 #pragma unroll
     for (int i = 0; i < NX; ++i) wx[i] = src[i * KP + k];
+    if constexpr (is_implicit<M>::value) {
+      if (k > 0) {  // row k's coefficient of x_k is A^+ (slot k); row 0's is I
+        const float* Ap = c.F(c.L.Ap);
+        double w2[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+          double acc = 0.0;
+#pragma unroll
+          for (int j = 0; j < NX; ++j) acc += (double)Ap[(j * NX + i) * KP + k] * wx[j];
+          w2[i] = acc;
+        }
+#pragma unroll
+        for (int i = 0; i < NX; ++i) wx[i] = w2[i];
+      }
+    }
     if (k < T) {
       double ln[NX];
 #pragma unroll
@@ -770,6 +899,21 @@ __device__ __noinline__ void hp_apply(Ctx<M, TEAM>& c, const double* src, bool r
 #pragma unroll
     for (int i = 0; i < NU; ++i) wu[i] = (k < T) ? WU[i * KP + k] : 0.0;
     c.ginv(k, wx, wu, s, su);
+    if constexpr (is_implicit<M>::value) {
+      if (k > 0) {
+        const float* Ap = c.F(c.L.Ap);
+        double s2[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+          double acc = 0.0;
+#pragma unroll
+          for (int j = 0; j < NX; ++j) acc += (double)Ap[(i * NX + j) * KP + k] * s[j];
+          s2[i] = acc;
+        }
+#pragma unroll
+        for (int i = 0; i < NX; ++i) s[i] = s2[i];
+      }
+    }
     if (k > 0) {
       const int t = k - 1;
       double vx[NX], vu[NU];
@@ -842,7 +986,16 @@ __device__ __noinline__ void df_apply(Ctx<M, TEAM>& c, const dfl* v, dfl* out, d
 #pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = 0; i < NX; ++i) {
       dacc a = dacc_zero();
-      dacc_add(a, v[i * KP + k]);
+      if constexpr (is_implicit<M>::value) {
+        if (k > 0) {
+#pragma unroll
+          for (int j = 0; j < NX; ++j) dacc_fma(a, c.F(c.L.Ap)[(j * NX + i) * KP + k], v[j * KP + k]);
+        } else {
+          dacc_add(a, v[i * KP + k]);
+        }
+      } else {
+        dacc_add(a, v[i * KP + k]);
+      }
       if (k < T) {
 #pragma unroll
         for (int j = 0; j < NX; ++j) dacc_fma(a, A[(j * NX + i) * KP + k + 1], v[j * KP + k + 1]);
@@ -871,7 +1024,17 @@ __device__ __noinline__ void df_apply(Ctx<M, TEAM>& c, const dfl* v, dfl* out, d
 #pragma unroll (NX <= 6 ? 32 : 1)
     for (int i = 0; i < NX; ++i) {
       dacc a = dacc_zero();
-      dacc_add(a, df_mul(WX[i * KP + k], k < T ? qx[i] : qT[i]));
+      if constexpr (is_implicit<M>::value) {
+        if (k > 0) {
+#pragma unroll
+          for (int j = 0; j < NX; ++j)
+            dacc_fma(a, c.F(c.L.Ap)[(i * NX + j) * KP + k], df_mul(WX[j * KP + k], k < T ? qx[j] : qT[j]));
+        } else {
+          dacc_add(a, df_mul(WX[i * KP + k], qx[i]));
+        }
+      } else {
+        dacc_add(a, df_mul(WX[i * KP + k], k < T ? qx[i] : qT[i]));
+      }
       if (k > 0) {
 #pragma unroll
         for (int j = 0; j < NX; ++j) dacc_fma(a, A[(i * NX + j) * KP + k], vx[j]);
@@ -1637,7 +1800,11 @@ __device__ __noinline__ int stage_pcg_warp(Ctx<M, 32>& c) {
     for (int i = 0; i < NX; ++i) e0[0] = fmaf(r[j][i], z[j][i], e0[0]);
   warp_sum(e0);
   const float eta0 = e0[0];
-  if (P.opt.pcg_precision == 1) return stage_pcg_warp_df<M, KPL>(c, eta0, P.opt.pcg_max_iters);
+  if (P.opt.pcg_precision == 1) {
+    // (the register double-float operator assumes A^+ = I; implicit models use the workspace one)
+    if constexpr (is_implicit<M>::value) return stage_pcg_df<M, 32>(c, eta0, P.opt.pcg_max_iters);
+    else return stage_pcg_warp_df<M, KPL>(c, eta0, P.opt.pcg_max_iters);
+  }
   // true residual of the initial guess, preconditioned residual, first direction
   hp_residual<M, 32>(c, LP);
 #pragma unroll
@@ -1730,7 +1897,8 @@ __device__ __noinline__ int stage_pcg_warp(Ctx<M, 32>& c) {
   }
   if (!converged) {
     c.status |= ST_FP64_RESCUE;
-    it += stage_pcg_warp_df<M, KPL>(c, eta0, maxit);
+    if constexpr (is_implicit<M>::value) it += stage_pcg_df<M, 32>(c, eta0, maxit);
+    else it += stage_pcg_warp_df<M, KPL>(c, eta0, maxit);
   }
   return it;
 }
@@ -1859,9 +2027,19 @@ __device__ __noinline__ float stage_linesearch(Ctx<M, TEAM>& c) {
           for (int i = 0; i < NX; ++i) xa[i] = X[i * KP + t] + a * (XP[i * KP + t] - X[i * KP + t]);
 #pragma unroll
           for (int i = 0; i < NU; ++i) ua[i] = U[i * KP + t] + a * (UP[i * KP + t] - U[i * KP + t]);
-          plain_step<M>(tk, pv, c.dt, xa, ua, xn);
+          if constexpr (is_implicit<M>::value) {
 #pragma unroll
-          for (int i = 0; i < NX; ++i) g += fabs((double)(X[i * KP + k] + a * (XP[i * KP + k] - X[i * KP + k])) - (double)xn[i]);
+            for (int i = 0; i < NX; ++i) xn[i] = X[i * KP + k] + a * (XP[i * KP + k] - X[i * KP + k]);
+            float rr[NX];
+            trap_residual<M>(xa, ua, xn, pv, c.dt, rr);
+#pragma unroll
+            for (int i = 0; i < NX; ++i) g += fabs((double)rr[i]);
+          } else {
+            plain_step<M>(tk, pv, c.dt, xa, ua, xn);
+#pragma unroll
+            for (int i = 0; i < NX; ++i)
+              g += fabs((double)(X[i * KP + k] + a * (XP[i * KP + k] - X[i * KP + k])) - (double)xn[i]);
+          }
         }
         red[11 + j] += g;
       }
@@ -2062,6 +2240,21 @@ __device__ __noinline__ void stage_bwd_rhs(Ctx<M, TEAM>& c) {
 #pragma unroll
     for (int i = 0; i < NU; ++i) gu[i] = (k < T) ? g[(long long)k * NZ + NX + i] : 0.f;
     c.ginv(k, gx, gu, s, su);
+    if constexpr (is_implicit<M>::value) {
+      if (k > 0) {  // row k's coefficient of x_k is A^+ (slot k)
+        const float* Ap = c.F(c.L.Ap);
+        double s2[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+          double acc = 0.0;
+#pragma unroll
+          for (int j = 0; j < NX; ++j) acc += (double)Ap[(i * NX + j) * KP + k] * s[j];
+          s2[i] = acc;
+        }
+#pragma unroll
+        for (int i = 0; i < NX; ++i) s[i] = s2[i];
+      }
+    }
     if (k > 0) {
       const int t = k - 1;
       double vx[NX], vu[NU];
@@ -2153,6 +2346,29 @@ __device__ __noinline__ void stage_bwd_finish(Ctx<M, TEAM>& c, int it) {
         for (int j = 0; j < NU; ++j) dk[NX * NX + i * NU + j] = li * UT[j * KP + t] + lti * U[j * KP + t];
         dk[NX * NX + NX * NU + i] = lti;
       }
+    } else if constexpr (is_implicit<M>::value) {
+      // f_t = x_{t+1} - x_t - h (F(x_t, u_t) + F(x_{t+1}, u_t)), h = dt/2: the contraction
+      // -(lambda^T f_{z theta} z~ + lambda~^T f_theta) = h sum over both evaluations of F
+      HDual<NP> xa[NX], xb[NX], uh[NU], ph[NP], fa[NX], fb[NX];
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        xa[i] = HDual<NP>(X[i * KP + t]); xa[i].e = XT[i * KP + t];
+        xb[i] = HDual<NP>(X[i * KP + k]); xb[i].e = XT[i * KP + k];
+      }
+#pragma unroll
+      for (int i = 0; i < NU; ++i) { uh[i] = HDual<NP>(U[i * KP + t]); uh[i].e = UT[i * KP + t]; }
+#pragma unroll
+      for (int j = 0; j < NP; ++j) { ph[j] = HDual<NP>(c.misc(MS_TH + j)); ph[j].t[j] = 1.f; }
+      M::f(xa, uh, ph, fa);
+      M::f(xb, uh, ph, fb);
+      const float h = 0.5f * c.dt;
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        const float li = h * (float)LAM[i * KP + k], lti = h * (float)LP[i * KP + k];
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+          red[j] = fmaf(li, fa[i].et[j] + fb[i].et[j], fmaf(lti, fa[i].t[j] + fb[i].t[j], red[j]));
+      }
     } else {
       HDual<NP> xh[NX], uh[NU], ph[NP], out[NX];
 #pragma unroll
@@ -2206,7 +2422,7 @@ __device__ __noinline__ void run_backward(Ctx<M, TEAM>& c) {
     stage_bwd_finish<M, TEAM>(c, 0);
     return;
   }
-  if (P.store_mode && P.store) {
+  if (P.store_mode && P.store && !is_implicit<M>::value) {  // stored records carry no A^+
     store_blocks<M, TEAM>(c, true);
   } else {
     stage_linearise<M, TEAM>(c);
@@ -2227,12 +2443,12 @@ __device__ void run_one(const KParams& P, int ocp, float* ws, int lane, int team
   c.T = c.o.T;
   c.K = c.o.T + 1;
   c.dt = c.o.dt;
-  c.L = make_layout(M::NX, M::NU, c.K, TEAM, P.opt.exact_hessian);
+  c.L = make_layout(M::NX, M::NU, c.K, TEAM, P.opt.exact_hessian, is_implicit<M>::value ? 1 : 0);
   c.KP = c.L.KP;
   c.db = reinterpret_cast<double*>(ws);
   c.fb = ws;
   c.status = 0;
-  c.exact = !is_lq<M>::value && P.opt.exact_hessian && P.mode == MODE_VJP;
+  c.exact = !is_lq<M>::value && !is_implicit<M>::value && P.opt.exact_hessian && P.mode == MODE_VJP;
   c.tm.lane = lane;
   c.tm.bar_id = team_in_block + 1;
   c.tm.red = ws + c.L.red;

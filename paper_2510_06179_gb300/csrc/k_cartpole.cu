@@ -7,5 +7,9 @@
 #endif
 
 namespace dmpc {
-int DMPC_REGISTER_NAME(cartpole, DMPC_TEAM)(KernelEntry* out) { return register_team<CartPole, DMPC_TEAM>(out, M_CARTPOLE); }
+int DMPC_REGISTER_NAME(cartpole, DMPC_TEAM)(KernelEntry* out) {
+  int n = register_team<CartPole, DMPC_TEAM>(out, M_CARTPOLE);
+  n += register_team<Trap<CartPole>, DMPC_TEAM>(out + n, M_CARTPOLE_TRAP);
+  return n;
+}
 }  // namespace dmpc

@@ -7,5 +7,9 @@
 #endif
 
 namespace dmpc {
-int DMPC_REGISTER_NAME(pendulum, DMPC_TEAM)(KernelEntry* out) { return register_team<Pendulum, DMPC_TEAM>(out, M_PENDULUM); }
+int DMPC_REGISTER_NAME(pendulum, DMPC_TEAM)(KernelEntry* out) {
+  int n = register_team<Pendulum, DMPC_TEAM>(out, M_PENDULUM);
+  n += register_team<Trap<Pendulum>, DMPC_TEAM>(out + n, M_PENDULUM_TRAP);
+  return n;
+}
 }  // namespace dmpc

@@ -1,7 +1,10 @@
 // Dynamics models f_t(x_{t+1}, x_t, u_t) = x_{t+1} - Phi_t(x_t, u_t; theta) of the OCP
 // (paper Sec. 3, OCP statement).  Each model gives continuous dynamics templated on the
 // scalar type (float, double, Dual<N>, HDual<P>) and an integrator; Phi_t is one
-// integrator step, so A_t^+ = I, A_t = -dPhi/dx, B_t = -dPhi/du in Eq. 4.
+// integrator step, so A_t^+ = I, A_t = -dPhi/dx, B_t = -dPhi/du in Eq. 4.  Trap<Model>
+// integrates the same continuous model by the implicit trapezoidal rule,
+// f_t = x_{t+1} - x_t - dt/2 (F(x_t, u_t) + F(x_{t+1}, u_t)), whose A_t^+ = I - dt/2 dF/dx(x_{t+1})
+// is a general matrix (Eq. 4 and 10 with A^+ != I).
 // The LQ model (affine x_{t+1} = Abar_t x_t + Bbar_t u_t + c_t, App. B.1) carries per-knot
 // parameters and is handled in closed form by the solver.
 #pragma once
@@ -11,9 +14,12 @@ namespace dmpc {
 
 enum ModelId : int {
   M_LQ = 0, M_PENDULUM = 1, M_CARTPOLE = 2, M_KIN_BICYCLE = 3,
-  M_SINGLE_TRACK = 4, M_RIGID_BODY12 = 5, M_ATTITUDE = 6
+  M_SINGLE_TRACK = 4, M_RIGID_BODY12 = 5, M_ATTITUDE = 6,
+  // internal ids of the trapezoidal (implicit) variants: model id + kTrapIdOffset
+  M_PENDULUM_TRAP = 17, M_CARTPOLE_TRAP = 18
 };
-enum Integrator : int { I_RK4 = 0, I_EULER = 1, I_AFFINE = 2 };
+constexpr int kTrapIdOffset = 16;
+enum Integrator : int { I_RK4 = 0, I_EULER = 1, I_AFFINE = 2, I_TRAP = 3 };
 
 constexpr float kGravity = 9.81f;
 
@@ -162,6 +168,24 @@ __device__ __forceinline__ void model_step(const S* x, const S* u, const S* p, f
   M::f(xt, u, p, k);
 #pragma unroll
   for (int i = 0; i < M::NX; ++i) xn[i] = x[i] + (dt / 6.0f) * (acc[i] + k[i]);
+}
+
+// A continuous model integrated by the implicit trapezoidal rule.
+template <class Base>
+struct Trap : Base {
+  static constexpr int ID = Base::ID + kTrapIdOffset, INTEG = I_TRAP;
+};
+
+template <class M> struct is_implicit { static constexpr bool value = M::INTEG == I_TRAP; };
+
+// f_t(x_t, u_t, x_{t+1}) of the trapezoidal rule.
+template <class M, class S>
+__device__ __forceinline__ void trap_residual(const S* x, const S* u, const S* xn, const S* p, float dt, S* r) {
+  S fa[M::NX], fb[M::NX];
+  M::f(x, u, p, fa);
+  M::f(xn, u, p, fb);
+#pragma unroll
+  for (int i = 0; i < M::NX; ++i) r[i] = (xn[i] - x[i]) - (0.5f * dt) * (fa[i] + fb[i]);
 }
 
 // The LQ model: per-knot Abar (nx*nx, row-major), Bbar (nx*nu), c (nx).  NX/NU are

@@ -79,7 +79,10 @@ bool shape_ok(const dmpc_ocp_desc& d, int* p_shared) {
     default: return false;
   }
   *p_shared = ps;
-  return d.nx == nx && d.nu == nu && d.T >= 1 && d.T <= 4096 &&
+  const bool integ_ok = d.integrator == DMPC_INTEGRATOR_DEFAULT ||
+                        (d.integrator == DMPC_INTEGRATOR_TRAPEZOID &&
+                         (d.model == DMPC_MODEL_PENDULUM || d.model == DMPC_MODEL_CARTPOLE));
+  return d.nx == nx && d.nu == nu && d.T >= 1 && d.T <= 4096 && integ_ok &&
          (d.model == DMPC_MODEL_LQ || (d.dt > 0.f && std::isfinite(d.dt)));
 }
 
@@ -106,7 +109,9 @@ extern "C" dmpc_err dmpc_solve_noalloc(const dmpc_ocp_desc* desc, int batch, con
   const int nx = desc->nx, nu = desc->nu, T = desc->T, K = T + 1;
   OcpRec proto;
   std::memset(&proto, 0, sizeof(proto));
-  proto.model = desc->model; proto.nx = nx; proto.nu = nu; proto.T = T; proto.dt = desc->dt;
+  const int implicit = desc->integrator == DMPC_INTEGRATOR_TRAPEZOID ? 1 : 0;
+  const int kmodel = implicit ? desc->model + kTrapIdOffset : desc->model;  // kernel-side id
+  proto.model = kmodel; proto.nx = nx; proto.nu = nu; proto.T = T; proto.dt = desc->dt;
   proto.n = K * nx + T * nu;
   proto.m = K * nx;
   proto.p = ps + T * (desc->model == DMPC_MODEL_LQ ? nx * nx + nx * nu + nx : 0) + 2 * nx + nu;
@@ -123,7 +128,7 @@ extern "C" dmpc_err dmpc_solve_noalloc(const dmpc_ocp_desc* desc, int batch, con
     else team = K <= 48 ? 32 : (K <= 160 ? 64 : (K <= 320 ? 128 : 256));
   }
   if (team != 32 && team != 64 && team != 128 && team != 256) return DMPC_E_ARG;
-  const int ws = make_layout(nx, nu, K, team, o.exact_hessian).total_floats;
+  const int ws = make_layout(nx, nu, K, team, o.exact_hessian, implicit).total_floats;
   const size_t ws_bytes = (size_t)ws * sizeof(float);
   const bool use_gws = ws_bytes > (size_t)smem_optin;
   const int max_tpb = 256 / team;
@@ -144,7 +149,7 @@ extern "C" dmpc_err dmpc_solve_noalloc(const dmpc_ocp_desc* desc, int batch, con
     KernelEntry table[kMaxKernelEntries];
     const int n = collect_kernel_entries(table);
     for (int i = 0; i < n; ++i)
-      if (table[i].team == team && table[i].model == desc->model && table[i].nx == nx && table[i].nu == nu) {
+      if (table[i].team == team && table[i].model == kmodel && table[i].nx == nx && table[i].nu == nu) {
         fn = table[i].fn;
         break;
       }

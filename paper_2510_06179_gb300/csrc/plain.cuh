@@ -228,8 +228,8 @@ __device__ void plain_one(const KParams& P, PlainState* st, int ocp, int step, i
   c.T = c.o.T;
   c.K = c.o.T + 1;
   c.dt = c.o.dt;
-  c.L = make_layout(M::NX, M::NU, c.K, TEAM, P.opt.exact_hessian);
-  c.exact = !is_lq<M>::value && P.opt.exact_hessian && P.mode == MODE_VJP;
+  c.L = make_layout(M::NX, M::NU, c.K, TEAM, P.opt.exact_hessian, is_implicit<M>::value ? 1 : 0);
+  c.exact = !is_lq<M>::value && !is_implicit<M>::value && P.opt.exact_hessian && P.mode == MODE_VJP;
   c.KP = c.L.KP;
   float* ws = P.gws + (size_t)ocp * P.ws_floats;
   c.db = reinterpret_cast<double*>(ws);

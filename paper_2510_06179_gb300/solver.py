@@ -13,6 +13,8 @@ from . import _lib
 from .workloads import MODELS
 
 MODEL_IDS = {k: v["id"] for k, v in MODELS.items()}
+# dmpc_integrator: the model's own step, or the implicit trapezoidal rule
+INTEGRATOR_IDS = {None: 0, "default": 0, "trapezoid": 1}
 
 
 def _ptr(t):
@@ -59,8 +61,10 @@ class OCPBatch:
         self.descs = [tuple(d) for d in descs]
         B = len(self.descs)
         arr = (_lib.dmpc_ocp_desc * B)()
-        for i, (model, nx, nu, T, dt) in enumerate(self.descs):
-            arr[i] = _lib.dmpc_ocp_desc(MODEL_IDS[model], nx, nu, T, dt)
+        for i, d in enumerate(self.descs):
+            model, nx, nu, T, dt = d[:5]
+            integ = INTEGRATOR_IDS[d[5] if len(d) > 5 else None]
+            arr[i] = _lib.dmpc_ocp_desc(MODEL_IDS[model], nx, nu, T, dt, integ)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.options = default_options(**options)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -161,7 +165,7 @@ class OCPBatch:
 
     def parse_inspect(self, rec, off, b):
         """Split OCP b's inspect record into named numpy arrays."""
-        model, nx, nu, T, dt = self.descs[b]
+        model, nx, nu, T, dt = self.descs[b][:5]
         K = T + 1
         r = rec[int(off[b]):int(off[b + 1])].detach().cpu().numpy().astype(np.float64)
         out, o = {}, 0

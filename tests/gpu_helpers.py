@@ -23,7 +23,7 @@ def make_batch(w, **opt):
     ensure_built()
     kw = dict(sqp_iters=w.sqp_iters, line_search=int(w.line_search), pcg_tol=1e-9)
     kw.update(opt)
-    return OCPBatch((w.model, w.nx, w.nu, w.T, w.dt), batch=w.B, device="cuda:0", **kw)
+    return OCPBatch((w.model, w.nx, w.nu, w.T, w.dt, w.integrator), batch=w.B, device="cuda:0", **kw)
 
 
 def gpu_solve(w, batch=None, **opt):
