@@ -83,7 +83,7 @@ def throughput(world, steps, seconds):
 # dram__bytes_read.sum + dram__bytes_write.sum of one forward launch from an ncu capture of this
 # bench step (the command and counters are summarised under profiles/), with the hash of the
 # kernel sources it was taken on; reported only while the sources still hash the same.
-TRAFFIC_CAPTURE = {"src_sha256_16": "2f927747e2c8a302", "bytes_per_launch": 691712 + 144896}
+TRAFFIC_CAPTURE = {"src_sha256_16": "5f931915f8163080", "bytes_per_launch": 625152 + 156160}
 
 
 def kernel_source_hash():
@@ -423,6 +423,15 @@ def main():
 
 
 # ---------------------------------------------------------------------- comparison suite
+def measured_hbm_gbs():
+    """Copy bandwidth measured on this machine's GPUs (MEASURED_PEAKS.json), else 6800 GB/s."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def _timed(fn, reps, warm=2):
     import torch
     for _ in range(warm):
@@ -481,6 +490,15 @@ def suite(path):
     dl = torch.zeros_like(z)
     dl.view(B, -1)[:, 4] = 1.0
     out["cartpole_b256"] = _fused_vs_plain(b, inp, dl, 5, B)
+    # the plain form against HBM: each of its PCG operations streams the S / Phi^-1 blocks and
+    # ~8 vectors of every OCP through HBM, 4 K (4 nx^2 + 8 nx) bytes per iteration per OCP
+    st = b.solve(*inp, plain=True)
+    iters = int(st["pcg_iters"].sum().item())
+    tp, tp_wall = _timed(lambda: b.solve(*inp, want_stats=False, plain=True), 1, warm=0)
+    pcg_bytes = iters * 4 * (T + 1) * (4 * 4 * 4 + 8 * 4)
+    gbs = pcg_bytes / max(tp, tp_wall) / 1e9
+    out["cartpole_b256"].update(plain_fwd_ms=max(tp, tp_wall) * 1e3, plain_pcg_bytes=pcg_bytes,
+                                plain_hbm_gbs=gbs, plain_hbm_frac=gbs / measured_hbm_gbs())
     b.close()
 
     # the same cart-pole batch with the implicit trapezoidal rule (A^+ != I)
