@@ -501,6 +501,22 @@ def suite(path):
                                 plain_hbm_gbs=gbs, plain_hbm_frac=gbs / measured_hbm_gbs())
     b.close()
 
+    # backward with the exact Lagrangian Hessian (FP64 Riccati) against the Gauss-Newton backward
+    # (adjoint PCG), on the same cart-pole batch at the same solution
+    ex = {}
+    for name, exact in (("gauss_newton", 0), ("exact_hessian", 1)):
+        b = OCPBatch(("cartpole", 4, 1, T, 0.05), batch=B, device=dev, sqp_iters=SQP_ITERS, line_search=1,
+                     pcg_tol=PCG_TOL, warm_start=0, exact_hessian=exact)
+        z = b.solve(*inp)["z"]
+        dl = torch.zeros_like(z)
+        dl.view(B, -1)[:, 4] = 1.0
+        tv, _ = _timed(lambda: b.vjp(dl, want_stats=False), 10)
+        st = b.vjp(dl)["status"]
+        ex[name + "_vjp_ms"] = tv * 1e3
+        ex[name + "_flagged"] = int(((st & 128) != 0).sum().item())
+        b.close()
+    out["cartpole_b256_backward"] = ex
+
     # the same cart-pole batch with the implicit trapezoidal rule (A^+ != I)
     w = workloads.cartpole_config(B=B, T=T, seed=1000, sqp_iters=SQP_ITERS, integrator="trapezoid")
     b = OCPBatch(("cartpole", 4, 1, T, 0.05, "trapezoid"), batch=B, device=dev, sqp_iters=SQP_ITERS,

@@ -1581,8 +1581,10 @@ __device__ __forceinline__ void warp_btmv_df(const float (&Md)[KPL][NX * NX], co
 
 template <class M, int KPL>
 __device__ __forceinline__ void warp_S_df(const float (&Ak)[KPL][M::NX * M::NX], const float (&Bk)[KPL][M::NX * M::NU],
+                                          const float (&Apk)[KPL][M::NX * M::NX],
                                           const dfl (&qi)[KPL][M::NX], const dfl (&ri)[M::NU], const bool (&has_u)[KPL],
                                           const dfl (&v)[KPL][M::NX], dfl (&out)[KPL][M::NX], int ln) {
+  // Apk: A^+ of the lane's knots (identity at knot 0); read only for implicit integrators
   constexpr int NX = M::NX, NU = M::NU;
   // pass 1: w = H^T v.  Knot k+1 owns A_k (slot k+1) and sends A_k^T v_{k+1}, B_k^T v_{k+1}.
   dfl t[KPL][NX], ub[KPL][NU];
@@ -1620,8 +1622,20 @@ __device__ __forceinline__ void warp_S_df(const float (&Ak)[KPL][M::NX * M::NX],
   dfl vx[KPL][NX], vu[KPL][NU];
 #pragma unroll
   for (int j = 0; j < KPL; ++j) {
+    dfl own[NX];  // the knot's own row term of H^T v: v_k, or A^+_k^T v_k for implicit integrators
 #pragma unroll
-    for (int i = 0; i < NX; ++i) vx[j][i] = df_mul(df_add(v[j][i], (j + 1 < KPL) ? t[j + 1 < KPL ? j + 1 : 0][i] : tn[i]), qi[j][i]);
+    for (int i = 0; i < NX; ++i) {
+      if constexpr (is_implicit<M>::value) {
+        dacc a = dacc_zero();
+#pragma unroll
+        for (int q = 0; q < NX; ++q) dacc_fma(a, Apk[j][q * NX + i], v[j][q]);
+        own[i] = dacc_get(a);
+      } else {
+        own[i] = v[j][i];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NX; ++i) vx[j][i] = df_mul(df_add(own[i], (j + 1 < KPL) ? t[j + 1 < KPL ? j + 1 : 0][i] : tn[i]), qi[j][i]);
 #pragma unroll
     for (int i = 0; i < NU; ++i)
       vu[j][i] = has_u[j] ? df_mul((j + 1 < KPL) ? ub[j + 1 < KPL ? j + 1 : 0][i] : ubn[i], ri[i]) : df_make(0.f);
@@ -1644,7 +1658,12 @@ __device__ __forceinline__ void warp_S_df(const float (&Ak)[KPL][M::NX * M::NX],
 #pragma unroll
     for (int i = 0; i < NX; ++i) {
       dacc a = dacc_zero();
-      dacc_add(a, vx[j][i]);
+      if constexpr (is_implicit<M>::value) {
+#pragma unroll
+        for (int q = 0; q < NX; ++q) dacc_fma(a, Apk[j][i * NX + q], vx[j][q]);
+      } else {
+        dacc_add(a, vx[j][i]);
+      }
 #pragma unroll
       for (int q = 0; q < NX; ++q) dacc_fma(a, Ak[j][i * NX + q], (j > 0) ? vx[j > 0 ? j - 1 : 0][q] : vxm[q]);
 #pragma unroll
@@ -1661,7 +1680,7 @@ __device__ __noinline__ int stage_pcg_warp_df(Ctx<M, 32>& c, float eta0f, int ma
   const int ln = c.tm.lane;
   double* LP = c.Dp(c.L.d_lamp);
   const double* G = c.Dp(c.L.d_gam);
-  float Pdk[KPL][NX * NX], Pok[KPL][NX * NX], Ak[KPL][NX * NX], Bk[KPL][NX * NU];
+  float Pdk[KPL][NX * NX], Pok[KPL][NX * NX], Ak[KPL][NX * NX], Bk[KPL][NX * NU], Apk[KPL][NX * NX];
   dfl qi[KPL][NX], ri[NU];
   bool live[KPL], has_u[KPL];
 #pragma unroll
@@ -1686,6 +1705,13 @@ __device__ __noinline__ int stage_pcg_warp_df(Ctx<M, 32>& c, float eta0f, int ma
 #pragma unroll
     for (int e = 0; e < NX * NU; ++e) Bk[j][e] = (live[j] && k > 0) ? c.F(c.L.Bm)[e * KP + k] : 0.f;
 #pragma unroll
+    for (int e = 0; e < NX * NX; ++e) {
+      if constexpr (is_implicit<M>::value)
+        Apk[j][e] = (k == 0) ? ((e / NX == e % NX) ? 1.f : 0.f) : (live[j] ? c.F(c.L.Ap)[e * KP + k] : 0.f);
+      else
+        Apk[j][e] = 0.f;
+    }
+#pragma unroll
     for (int i = 0; i < NX; ++i) qi[j][i] = live[j] ? df_from(c.qinv(k, i)) : df_make(0.f);
   }
 #pragma unroll
@@ -1698,7 +1724,7 @@ __device__ __noinline__ int stage_pcg_warp_df(Ctx<M, 32>& c, float eta0f, int ma
 #pragma unroll
     for (int i = 0; i < NX; ++i) x[j][i] = live[j] ? df_from(LP[i * KP + ln * KPL + j]) : df_make(0.f);
   // r = gamma - S x, z = Phi^-1 r, p = z, eta = r^T z
-  warp_S_df<M, KPL>(Ak, Bk, qi, ri, has_u, x, y, ln);
+  warp_S_df<M, KPL>(Ak, Bk, Apk, qi, ri, has_u, x, y, ln);
 #pragma unroll
   for (int j = 0; j < KPL; ++j)
 #pragma unroll
@@ -1713,7 +1739,7 @@ __device__ __noinline__ int stage_pcg_warp_df(Ctx<M, 32>& c, float eta0f, int ma
   int it = 0;
   bool converged = !(eta.hi > thr.hi);
   while (!converged && it < maxit) {
-    warp_S_df<M, KPL>(Ak, Bk, qi, ri, has_u, p, y, ln);
+    warp_S_df<M, KPL>(Ak, Bk, Apk, qi, ri, has_u, p, y, ln);
     dacc va = dacc_zero();
 #pragma unroll
     for (int j = 0; j < KPL; ++j)
@@ -1800,11 +1826,7 @@ __device__ __noinline__ int stage_pcg_warp(Ctx<M, 32>& c) {
     for (int i = 0; i < NX; ++i) e0[0] = fmaf(r[j][i], z[j][i], e0[0]);
   warp_sum(e0);
   const float eta0 = e0[0];
-  if (P.opt.pcg_precision == 1) {
-    // (the register double-float operator assumes A^+ = I; implicit models use the workspace one)
-    if constexpr (is_implicit<M>::value) return stage_pcg_df<M, 32>(c, eta0, P.opt.pcg_max_iters);
-    else return stage_pcg_warp_df<M, KPL>(c, eta0, P.opt.pcg_max_iters);
-  }
+  if (P.opt.pcg_precision == 1) return stage_pcg_warp_df<M, KPL>(c, eta0, P.opt.pcg_max_iters);
   // true residual of the initial guess, preconditioned residual, first direction
   hp_residual<M, 32>(c, LP);
 #pragma unroll
@@ -1897,8 +1919,7 @@ __device__ __noinline__ int stage_pcg_warp(Ctx<M, 32>& c) {
   }
   if (!converged) {
     c.status |= ST_FP64_RESCUE;
-    if constexpr (is_implicit<M>::value) it += stage_pcg_df<M, 32>(c, eta0, maxit);
-    else it += stage_pcg_warp_df<M, KPL>(c, eta0, maxit);
+    it += stage_pcg_warp_df<M, KPL>(c, eta0, maxit);
   }
   return it;
 }
