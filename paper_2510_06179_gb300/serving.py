@@ -150,6 +150,15 @@ class SlotClass:
         return len(done)
 
 
+def class_priorities(shapes):
+    """Stream priority per class (model, T bucket): cheaper classes (smaller nx^2 T) get higher
+    priority (more negative; torch clamps to the device's range), so their blocks are scheduled
+    first whenever heavier classes' blocks leave room on an SM."""
+    costs = sorted({nx * nx * hi for _, nx, _, _ in shapes for _, hi in T_BUCKETS})
+    return {(model, lo, hi): -(len(costs) - 1 - costs.index(nx * nx * hi))
+            for model, nx, _, _ in shapes for lo, hi in T_BUCKETS}
+
+
 class ServingEngine:
     """Slot classes by (model, horizon bucket) under a device-memory budget."""
 
@@ -163,13 +172,10 @@ class ServingEngine:
         opts.update(options)
         self.classes = {}
         used = 0
-        # cheaper classes (smaller nx^2 T) get higher stream priority, so their blocks are
-        # scheduled first whenever heavier classes' blocks leave room on an SM
-        costs = sorted({nx * nx * hi for _, nx, _, _ in shapes for _, hi in T_BUCKETS})
+        prios = class_priorities(shapes)
         for model, nx, nu, dt in shapes:
             for lo, hi in T_BUCKETS:
-                prio = -(len(costs) - 1 - costs.index(nx * nx * hi))   # torch clamps to the device range
-                c = SlotClass(model, nx, nu, lo, hi, dt, slots_per_class, opts, self.device, prio)
+                c = SlotClass(model, nx, nu, lo, hi, dt, slots_per_class, opts, self.device, prios[(model, lo, hi)])
                 c.batch.sqp_iters_total = sqp_iters
                 used += int(self.lib_bytes(c))
                 self.classes[(model, lo, hi)] = c

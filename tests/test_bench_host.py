@@ -39,3 +39,16 @@ def test_branch_classification_and_gates():
     assert acc["agree_within_gates"] == 1
     assert abs(acc["z_rel_err_max_agree"] - 1e-3) < 1e-9
     assert acc["z_within_1e-4_all"] == 3
+
+
+def test_serving_class_priorities_order_by_cost():
+    """Cheaper serving classes get higher (more negative) stream priority; the most expensive
+    class gets the default priority 0."""
+    from paper_2510_06179_gb300 import workloads
+    from paper_2510_06179_gb300.serving import class_priorities, T_BUCKETS
+    pr = class_priorities(workloads.SERVING_SHAPES)
+    cost = {(m, lo, hi): nx * nx * hi for m, nx, _, _ in workloads.SERVING_SHAPES for lo, hi in T_BUCKETS}
+    keys = sorted(pr, key=lambda k: cost[k])
+    assert pr[keys[-1]] == 0
+    assert all(pr[a] <= pr[b] for a, b in zip(keys, keys[1:]))
+    assert pr[keys[0]] < 0
