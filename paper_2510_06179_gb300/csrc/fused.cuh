@@ -1934,6 +1934,8 @@ __device__ __forceinline__ int run_pcg(Ctx<M, TEAM>& c) {
     } else {
       if (c.K <= TEAM) return stage_pcg_reg<M, TEAM>(c);
     }
+  } else if constexpr (M::NX <= 6 && TEAM > 32) {
+    if (c.K <= TEAM) return stage_pcg_reg<M, TEAM>(c);
   }
   return stage_pcg<M, TEAM>(c);
 }
