@@ -1,0 +1,51 @@
+"""Parity at the benchmark's full sizes and launch configuration, on sampled OCPs the oracle
+solves one by one: cart-pole (256 OCPs, T 50, 10 SQP iterations, tolerance 1e-7, default tiling,
+solution and gradient) and the single-track vehicle (1024 OCPs, T 100)."""
+import numpy as np
+import pytest
+
+from paper_2510_06179_gb300 import workloads
+from oracle.backward import vjp as oracle_vjp
+from oracle.sqp import sqp as oracle_sqp
+from tests.gpu_helpers import gpu_solve, gpu_vjp, alpha_paths_agree
+from tests.oracle_helpers import to_ocp, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _sampled(w, g, idx):
+    sub = w.subset(idx)
+    ref = oracle_sqp(to_ocp(sub), w.sqp_iters, line_search_on=True)
+    agree = alpha_paths_agree(g["alpha"][idx], ref["alpha"])
+    e = rel_err(g["z"][idx], ref["z"])
+    return sub, ref, agree, e
+
+
+def test_cartpole_bench_configuration_sampled():
+    w = workloads.cartpole_config(B=256, T=50, seed=1000, sqp_iters=10)
+    b, g = gpu_solve(w, pcg_tol=1e-7, warm_start=0)
+    idx = np.random.default_rng(0).choice(256, size=24, replace=False)
+    sub, ref, agree, e = _sampled(w, g, idx)
+    print(f"cart-pole 256: sampled {len(idx)}, agree {agree.sum()}, max err agreeing {e[agree].max():.2e}")
+    assert agree.mean() >= 0.7
+    assert e[agree].max() <= 1e-4
+    # gradient at the GPU's solution (the backward isolated from the forward's error)
+    dl = w.dl_dz(g["z"])
+    gv = gpu_vjp(b, w, dl)
+    gref = oracle_vjp(to_ocp(sub), g["z"][idx], g["lam"][idx], dl[idx])
+    ge = rel_err(gv["dtheta"][idx], gref["dtheta"])
+    print(f"cart-pole 256: sampled gradient max err {ge.max():.2e}")
+    assert ge.max() <= 1e-3
+    b.close()
+
+
+def test_vehicle_full_batch_sampled():
+    w = workloads.vehicle_config(B=1024, T=100, seed=0, sqp_iters=10)
+    b, g = gpu_solve(w, pcg_tol=1e-7, warm_start=0)
+    idx = np.random.default_rng(1).choice(1024, size=6, replace=False)
+    sub, ref, agree, e = _sampled(w, g, idx)
+    print(f"vehicle 1024: sampled {len(idx)}, agree {agree.sum()}, errors {e}")
+    assert agree.sum() >= 2
+    assert e[agree].max() <= 1e-4
+    assert not (g["status"] & (1 | 2 | 8)).any()
+    b.close()
