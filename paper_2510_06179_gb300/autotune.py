@@ -26,7 +26,7 @@ TPBS = (1, 2, 4, 8)
 
 def signature(batch):
     """Cache key: model mix, horizon range (power-of-two buckets), batch bucket, SM count."""
-    models = sorted({(d[0], d[1], d[2]) for d in batch.descs})
+    models = sorted({(d[0], d[1], d[2], d[5] if len(d) > 5 and d[5] else "") for d in batch.descs})
     Ts = [d[3] for d in batch.descs]
     lo, hi = 2 ** int(math.log2(min(Ts))), 2 ** int(math.ceil(math.log2(max(Ts) + 1)))
     bbucket = 2 ** int(math.ceil(math.log2(batch.B)))
