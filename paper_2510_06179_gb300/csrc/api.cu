@@ -215,11 +215,11 @@ static dmpc_err configure_tiling(dmpc_handle* h, int team, int tpb) {
   if (team == 0) {
     // one knot per lane (register-resident PCG) when it fits, else a few knots per lane:
     // nx <= 4: one warp with one or two knots per lane up to K = 64; nx <= 6: one knot per lane
-    // (64 to 256 threads); larger nx: shared-memory PCG, 128 threads from K = 49 on
+    // (64 to 256 threads); larger nx: shared-memory PCG with 32 / 64 / 128 threads by K
     if (maxnx <= 6 && maxK <= 256)
       team = maxK <= 64 ? (maxnx <= 4 ? 32 : 64) : (maxK <= 128 ? 128 : 256);
     else
-      team = maxK <= 48 ? 32 : (maxK <= 320 ? 128 : 256);
+      team = maxK <= 32 ? 32 : (maxK <= 64 ? 64 : (maxK <= 320 ? 128 : 256));
   }
   int ws = 0;
   for (auto& d : h->descs) ws = std::max(ws, make_layout(d.nx, d.nu, d.T + 1, team, h->opt.exact_hessian, is_implicit_desc(d)).total_floats);
