@@ -47,3 +47,30 @@ def closed_loop_reward(batch, prob, q, env=None):
 def env_tensors(prob, device):
     t = lambda a: torch.from_numpy(a).to(device)
     return t(prob.A), t(prob.Bm), t(prob.b), t(prob.x0), t(prob.knot_theta())
+
+
+class RolloutGraph:
+    """The forward closed-loop rollout (no gradients) captured once as a CUDA graph: the H solves
+    and the environment steps between them replay with a single graph launch, removing the
+    per-step host dispatch that bounds the eager rollout.  replay(q) copies new cost weights into
+    the captured input and returns the reward tensor (valid after synchronisation)."""
+
+    def __init__(self, batch, prob, q, env=None, warmup=2):
+        self.batch, self.prob = batch, prob
+        self.env = env if env is not None else env_tensors(prob, q.device)
+        self.q = q.detach().clone()
+        s = torch.cuda.Stream(q.device)
+        s.wait_stream(torch.cuda.current_stream(q.device))
+        with torch.cuda.stream(s), torch.no_grad():
+            for _ in range(warmup):
+                closed_loop_reward(batch, prob, self.q, self.env)
+        torch.cuda.current_stream(q.device).wait_stream(s)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph), torch.no_grad():
+            self.reward = closed_loop_reward(batch, prob, self.q, self.env)
+
+    def replay(self, q=None):
+        if q is not None:
+            self.q.copy_(q)
+        self.graph.replay()
+        return self.reward

@@ -87,3 +87,27 @@ def test_one_handle_for_many_solves_equals_separate_handles():
     assert np.allclose(grads[0], grads[1], rtol=1e-5, atol=1e-6 * np.abs(grads[1]).max())
     for b in (one,) + two:
         b.close()
+
+
+def test_graph_captured_rollout_matches_eager():
+    import torch
+    from paper_2510_06179_gb300.rollout import make_batch, closed_loop_reward, RolloutGraph, env_tensors
+    ensure_built()
+    prob = workloads.rl_lq_problem(2, seed=5, B=8, H=6, T=12)
+    dev = "cuda:0"
+    env = env_tensors(prob, dev)
+    b1 = make_batch(prob, dev)
+    q = torch.from_numpy(prob.q0.copy()).to(dev)
+    with torch.no_grad():
+        r_eager = float(closed_loop_reward(b1, prob, q, env).item())
+    b2 = make_batch(prob, dev)
+    g = RolloutGraph(b2, prob, q, env)
+    q2 = q * 1.1
+    with torch.no_grad():
+        r_eager2 = float(closed_loop_reward(b1, prob, q2, env).item())
+    r_graph2 = float(g.replay(q2).item())
+    r_graph = float(g.replay(q).item())
+    assert abs(r_graph - r_eager) <= 1e-5 * abs(r_eager)
+    assert abs(r_graph2 - r_eager2) <= 1e-5 * abs(r_eager2)
+    b1.close()
+    b2.close()
