@@ -182,54 +182,54 @@ __device__ __forceinline__ void btmv_row(const float* Md, const float* Mo, const
 template <int NX, class V = float>
 __device__ bool spd_inverse(const V* a, V* inv) {
   V L[NX * NX];
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
   for (int i = 0; i < NX * NX; ++i) L[i] = V(0);
   bool ok = true;
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
   for (int j = 0; j < NX; ++j) {
     V s = a[j * NX + j];
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int k = 0; k < j; ++k) s -= L[j * NX + k] * L[j * NX + k];
     if (!(s > V(0))) { ok = false; s = fabs(a[j * NX + j]) + V(1e-30); }
     const V d = sqrt(s);
     L[j * NX + j] = d;
     const V id = V(1) / d;
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = j + 1; i < NX; ++i) {
       V t = a[i * NX + j];
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
       for (int k = 0; k < j; ++k) t -= L[i * NX + k] * L[j * NX + k];
       L[i * NX + j] = t * id;
     }
   }
   if (!ok) {
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NX * NX; ++i) inv[i] = V(0);
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NX; ++i) inv[i * NX + i] = V(1) / (fabs(a[i * NX + i]) + V(1e-30));
     return false;
   }
   // W = L^-1 (lower triangular), forward substitution column by column
   V W[NX * NX];
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
   for (int i = 0; i < NX * NX; ++i) W[i] = V(0);
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
   for (int c = 0; c < NX; ++c) {
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = c; i < NX; ++i) {
       V t = (i == c) ? V(1) : V(0);
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
       for (int k = c; k < i; ++k) t -= L[i * NX + k] * W[k * NX + c];
       W[i * NX + c] = t / L[i * NX + i];
     }
   }
   // inv = W^T W
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
   for (int i = 0; i < NX; ++i) {
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int j = 0; j <= i; ++j) {
       V s = V(0);
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
       for (int k = (i > j ? i : j); k < NX; ++k) s += W[k * NX + i] * W[k * NX + j];
       inv[i * NX + j] = s;
       inv[j * NX + i] = s;
@@ -673,15 +673,15 @@ __device__ __noinline__ void stage_schur(Ctx<M, TEAM>& c, bool rhs_from_qp) {
   const float* xs = P.x_s + c.o.xs_off;
   for (int k = c.tm.lane; k < K; k += TEAM) {
     float qi[NX];
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NX; ++i) qi[i] = 1.f / c.qproj(k, i);
     if (k == 0) {
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
       for (int i = 0; i < NX; ++i)
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
         for (int j = 0; j < NX; ++j) D[(i * NX + j) * KP] = (i == j) ? qi[i] : 0.f;
       if (rhs_from_qp) {
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
         for (int i = 0; i < NX; ++i)
           G[i * KP] = -(double)xs[i] - c.qlin(0, i, X[i * KP]) * c.qinv(0, i);
       }
@@ -746,42 +746,42 @@ __device__ __noinline__ void stage_schur(Ctx<M, TEAM>& c, bool rhs_from_qp) {
       continue;
     }
     float qt[NX], ri[NU];
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NX; ++i) qt[i] = 1.f / c.qproj(t, i);
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NU; ++i) ri[i] = 1.f / c.misc(MS_RP + i);
     float a[NX * NX], b[NX * NU];
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NX * NX; ++i) a[i] = A[i * KP + k];
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NX * NU; ++i) b[i] = Bm[i * KP + k];
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NX; ++i) {
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
       for (int j = 0; j <= i; ++j) {
         float s = (i == j) ? qi[i] : 0.f;
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
         for (int l = 0; l < NX; ++l) s = fmaf(a[i * NX + l] * qt[l], a[j * NX + l], s);
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
         for (int l = 0; l < NU; ++l) s = fmaf(b[i * NU + l] * ri[l], b[j * NU + l], s);
         D[(i * NX + j) * KP + k] = s;
         D[(j * NX + i) * KP + k] = s;
       }
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
       for (int j = 0; j < NX; ++j) O[(i * NX + j) * KP + k] = a[i * NX + j] * qt[j];
     }
     if (rhs_from_qp) {
       double vq[NX], vr[NU];
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
       for (int j = 0; j < NX; ++j) vq[j] = c.qlin(t, j, X[j * KP + t]) * c.qinv(t, j);
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
       for (int j = 0; j < NU; ++j) vr[j] = c.rlin(j, U[j * KP + t]) * c.rinv(j);
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
       for (int i = 0; i < NX; ++i) {
         double z = c.qlin(k, i, X[i * KP + k]) * c.qinv(k, i);
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
         for (int j = 0; j < NX; ++j) z += (double)a[i * NX + j] * vq[j];
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
         for (int j = 0; j < NU; ++j) z += (double)b[i * NU + j] * vr[j];
         G[i * KP + k] = -(double)C[i * KP + k] - z;
       }
@@ -801,10 +801,10 @@ __device__ __noinline__ void stage_precond(Ctx<M, TEAM>& c) {
   float* Po = c.F(c.L.Po);
   for (int k = c.tm.lane; k < K; k += TEAM) {
     float a[NX * NX], inv[NX * NX];
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NX * NX; ++i) a[i] = D[i * KP + k];
     if (!spd_inverse<NX>(a, inv)) c.status |= ST_CHOL_FAIL;
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NX * NX; ++i) Pd[i * KP + k] = inv[i];
   }
   c.tm.sync();
@@ -812,21 +812,21 @@ __device__ __noinline__ void stage_precond(Ctx<M, TEAM>& c) {
     if (k == 0) continue;
     float t1[NX * NX];
     // t1 = O_k Pd_{k-1}
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NX; ++i)
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
       for (int j = 0; j < NX; ++j) {
         float s = 0.f;
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
         for (int l = 0; l < NX; ++l) s = fmaf(O[(i * NX + l) * KP + k], Pd[(l * NX + j) * KP + k - 1], s);
         t1[i * NX + j] = s;
       }
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NX; ++i)
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
       for (int j = 0; j < NX; ++j) {
         float s = 0.f;
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
         for (int l = 0; l < NX; ++l) s = fmaf(Pd[(i * NX + l) * KP + k], t1[l * NX + j], s);
         Po[(i * NX + j) * KP + k] = -s;
       }
@@ -983,7 +983,7 @@ __device__ __noinline__ void df_apply(Ctx<M, TEAM>& c, const dfl* v, dfl* out, d
   const float* Bm = c.F(c.L.Bm);
   c.tm.sync();
   for (int k = c.tm.lane; k < K; k += TEAM) {
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NX; ++i) {
       dacc a = dacc_zero();
       if constexpr (is_implicit<M>::value) {
@@ -1021,7 +1021,7 @@ __device__ __noinline__ void df_apply(Ctx<M, TEAM>& c, const dfl* v, dfl* out, d
 #pragma unroll
       for (int j = 0; j < NU; ++j) vu[j] = df_mul(WU[j * KP + k - 1], ri[j]);
     }
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NX; ++i) {
       dacc a = dacc_zero();
       if constexpr (is_implicit<M>::value) {
@@ -1050,7 +1050,7 @@ __device__ __noinline__ void df_apply(Ctx<M, TEAM>& c, const dfl* v, dfl* out, d
 template <int NX>
 __device__ __forceinline__ void btmv_row_df(const float* Md, const float* Mo, const dfl* v, int k, int K, int KP,
                                             dfl (&out)[NX]) {
-#pragma unroll (NX <= 6 ? 32 : 1)
+#pragma unroll (NX <= 8 ? 32 : 1)
   for (int i = 0; i < NX; ++i) {
     dacc a = dacc_zero();
 #pragma unroll
