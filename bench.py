@@ -671,7 +671,9 @@ def reference_arm(args, rank, world):
     line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "batch_per_step": n},
+            "config": {"workload": WORKLOAD, "batch_per_gpu": B, "T": T, "sqp_iters": SQP_ITERS,
+                       "ocps_per_step": n, "solver": "FP64 oracle, direct KKT solves (no PCG tolerance)",
+                       "parallelism": f"{cores} host processes"},
             "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{n} of the 256 OCPs per step, FP64, {cores} processes x 1 thread"},
             "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
