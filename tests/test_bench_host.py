@@ -1,5 +1,5 @@
-"""Host logic of the benchmark's accuracy report (no GPU): gating of agreeing step-size
-paths and the near-tie classification of branched ones."""
+"""Host logic of the benchmark (no GPU): gating of agreeing step-size paths and the near-tie
+classification of branched ones in the accuracy report, and the reference arm's output line."""
 import numpy as np
 
 import bench
@@ -52,3 +52,26 @@ def test_serving_class_priorities_order_by_cost():
     assert pr[keys[-1]] == 0
     assert all(pr[a] <= pr[b] for a, b in zip(keys, keys[1:]))
     assert pr[keys[0]] < 0
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` (the FP64 oracle on the host cores) needs no GPU and prints
+    one JSON line with the contract's keys, on the same workload as the GPU line."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3",
+                        "--cpu-sample", "2"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == bench.UNIT and d["metric"] == bench.METRIC
+    assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    cfg = d["config"]
+    assert cfg["workload"] == bench.WORKLOAD and cfg["batch_per_gpu"] == bench.B and cfg["T"] == bench.T
+    assert cfg["sqp_iters"] == bench.SQP_ITERS and cfg["ocps_per_step"] == 2
