@@ -1,6 +1,7 @@
 """Edge cases on the GPU: the maximum horizon the boundary accepts (T = 4096, workspace in
-global memory), a one-OCP batch with an implicit integrator and T = 1, and an empty subset
-launch of the serving entry point (a no-op that leaves the resident state alone)."""
+global memory), a large batch (100 000 OCPs in one launch, sampled against the oracle), a
+one-OCP batch with an implicit integrator and T = 1, and an empty subset launch of the serving
+entry point (a no-op that leaves the resident state alone)."""
 import ctypes
 
 import numpy as np
@@ -24,6 +25,23 @@ def test_maximum_horizon_matches_oracle():
     print(f"T=4096: agree {agree.sum()}/2 err {e}")
     assert agree.any() and e[agree].max() <= 1e-4
     assert not (g["status"] & (1 | 2 | 8)).any()
+    b.close()
+
+
+def test_large_batch_sampled_against_oracle():
+    w = workloads.pendulum_config(B=100_000, T=8, seed=11, sqp_iters=2)
+    b, g = gpu_solve(w)
+    t = b.get_tiling()
+    print(f"B=100000: tiling {t}")
+    assert t["grid"] * t["teams_per_block"] >= w.B
+    assert not (g["status"] & (1 | 2 | 8)).any()
+    idx = np.concatenate([np.arange(3), np.random.default_rng(2).choice(w.B, size=5, replace=False), [w.B - 1]])
+    sub = w.subset(idx)
+    ref = oracle_sqp(to_ocp(sub), w.sqp_iters, line_search_on=True)
+    agree = alpha_paths_agree(g["alpha"][idx], ref["alpha"])
+    e = rel_err(g["z"][idx], ref["z"])
+    print(f"B=100000: sampled {len(idx)}, agree {agree.sum()}, errors {e}")
+    assert agree.sum() >= 6 and e[agree].max() <= 1e-4
     b.close()
 
 
