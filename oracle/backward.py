@@ -14,7 +14,7 @@ dl/dx_s = lambda~_0, because dg_0/dx_s = -I.
 """
 import numpy as np
 
-from .ocp import (linearise, solve_qp, split_z, join_z, split_theta, theta_offsets,
+from .ocp import (linearise, solve_qp, split_z, split_theta, theta_offsets,
                   dynamics_jet, constraint_jet, x_index, u_index)
 
 

@@ -4,7 +4,6 @@ Each .cu translation unit compiles in parallel; the objects link into one shared
 with the C-ABI of include/dmpc.h."""
 import os
 import subprocess
-import sys
 from concurrent.futures import ThreadPoolExecutor
 
 PKG = os.path.dirname(os.path.abspath(__file__))

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2510_06179_gb300 import workloads
-from tests.gpu_helpers import make_batch, gpu_solve, gpu_vjp, dev, ensure_built
+from tests.gpu_helpers import make_batch, dev, ensure_built
 from tests.oracle_helpers import rel_err
 
 pytestmark = pytest.mark.gpu

@@ -7,8 +7,8 @@ import numpy as np
 import pytest
 
 from paper_2510_06179_gb300 import workloads
-from tests.gpu_helpers import gpu_solve, gpu_vjp, dev
-from tests.oracle_helpers import to_ocp, rel_err
+from tests.gpu_helpers import gpu_solve, dev
+from tests.oracle_helpers import rel_err
 from tests.test_gpu_parity import _check_inspect, _nonlinear_forward, _grad_check
 
 pytestmark = pytest.mark.gpu

@@ -4,7 +4,6 @@ process groups on the CPU."""
 import os
 import socket
 
-import pytest
 import torch.multiprocessing as mp
 
 

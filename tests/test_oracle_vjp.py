@@ -3,7 +3,6 @@ differences of the loss: exact for affine dynamics (LQ) with the Gauss-Newton KK
 and exact on nonlinear dynamics with the exact-Hessian KKT matrix; the Gauss-Newton gap on
 nonlinear dynamics (Sec. 3.4) is measured, not gated."""
 import numpy as np
-import pytest
 
 from paper_2510_06179_gb300 import workloads
 from oracle import ocp as O
