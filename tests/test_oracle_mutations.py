@@ -1,0 +1,156 @@
+"""The oracle's pins catch plausible mistakes: each case plants one mistake in the oracle (a
+transposed block, a flipped sign, a dropped term, a wrong constant), on the CPU and only for
+the duration of the test, and checks that the pin written against it now fails.  A pin that
+still passed under its mutation would not be pinning anything."""
+import dataclasses
+import sys
+
+import numpy as np
+import pytest
+
+from oracle import backward as BW
+from oracle import models as MD
+from oracle import ocp as O
+from oracle import schur as S
+from oracle import sqp as SQ
+from tests import test_oracle_kkt as KKT
+from tests import test_oracle_models as MODELS
+from tests import test_oracle_sqp as SQP
+from tests import test_oracle_vjp as VJP
+
+
+def _patch_all(monkeypatch, owner, name, new):
+    """Replace `owner.name` in every loaded module that holds the same object (the oracle's
+    modules import each other's functions by name)."""
+    orig = getattr(owner, name)
+    for mod in list(sys.modules.values()):
+        if mod is not None and getattr(mod, name, None) is orig:
+            monkeypatch.setattr(mod, name, new)
+    return orig
+
+
+def _schur_offdiag_transposed(mp):
+    orig = S.schur_blocks
+
+    def mutant(qp):
+        D, Off = orig(qp)
+        return D, np.swapaxes(Off, -1, -2)
+    _patch_all(mp, S, "schur_blocks", mutant)
+
+
+def _preconditioner_offdiag_sign(mp):
+    orig = S.preconditioner_blocks
+
+    def mutant(D, Off):
+        Dinv, P = orig(D, Off)
+        return Dinv, -P
+    _patch_all(mp, S, "preconditioner_blocks", mutant)
+
+
+def _gamma_drops_next_knot_term(mp):
+    orig = S.gamma_spd
+
+    def mutant(qp, q=None, r=None, d=None):
+        g = orig(qp, q, r, d).copy()
+        qq = qp.q if q is None else q
+        g[:, 1:] += np.einsum("btij,btj->bti", qp.Ap, qq[:, 1:] / qp.Q[:, 1:])
+        return g
+    _patch_all(mp, S, "gamma_spd", mutant)
+
+
+def _recovery_sign(mp):
+    orig = S.recover_primal
+
+    def mutant(qp, lam, q=None, r=None):
+        x, u = orig(qp, lam, q, r)
+        return -x, -u
+    _patch_all(mp, S, "recover_primal", mutant)
+
+
+def _linearise_drops_delta_form(mp):
+    orig = O.linearise
+
+    def mutant(ocp, z):
+        qp = orig(ocp, z)
+        x, _ = O.split_z(ocp, z)
+        return dataclasses.replace(qp, q=qp.q + qp.Q * x)
+    _patch_all(mp, O, "linearise", mutant)
+
+
+def _kkt_rhs_constraint_sign(mp):
+    orig = O.kkt_rhs
+
+    def mutant(qp, b):
+        mb, d = orig(qp, b)
+        return mb, -d
+    _patch_all(mp, O, "kkt_rhs", mutant)
+
+
+def _merit_constraint_norm_doubled(mp):
+    orig = SQ.merit_parts
+
+    def mutant(ocp, z):
+        c, g = orig(ocp, z)
+        return c, 2.0 * g
+    _patch_all(mp, SQ, "merit_parts", mutant)
+
+
+def _rk4_weights(mp):
+    def mutant(fc, x, u, ths, dt):
+        k1 = fc(x, u, ths)
+        k2 = fc([xi + 0.5 * dt * ki for xi, ki in zip(x, k1)], u, ths)
+        k3 = fc([xi + 0.5 * dt * ki for xi, ki in zip(x, k2)], u, ths)
+        k4 = fc([xi + dt * ki for xi, ki in zip(x, k3)], u, ths)
+        return [xi + (dt / 4.0) * (a + b + c + d) for xi, a, b, c, d in zip(x, k1, k2, k3, k4)]
+    _patch_all(mp, MD, "rk4", mutant)
+
+
+def _cartpole_gravity_sign(mp):
+    def mutant(self, x, u, ths):
+        p, v, phi, w = x
+        m_p, L = ths
+        s, c = MD.sin(phi), MD.cos(phi)
+        den = self.m_c + m_p * s * s
+        pdd = (u[0] + m_p * s * (L * w * w - MD.GRAVITY * c)) / den
+        wdd = (-(self.m_c + m_p) * MD.GRAVITY * s - u[0] * c - m_p * L * w * w * s * c) / (L * den)
+        return [v, pdd, w, wdd]
+    mp.setattr(MD.CartPole, "fc", mutant)
+
+
+def _backward_drops_mixed_term(mp):
+    orig = BW._phi_jets
+
+    def mutant(ocp, z):
+        g, h = orig(ocp, z)
+        return g, np.zeros_like(h)
+    _patch_all(mp, BW, "_phi_jets", mutant)
+
+
+CASES = {
+    "Schur off-diagonal block transposed (Eq. 10)": (_schur_offdiag_transposed,
+                                                     lambda: KKT.test_schur_blocks_match_dense("lq")),
+    "preconditioner off-diagonal sign (Eq. 10)": (_preconditioner_offdiag_sign,
+                                                  KKT.test_preconditioner_matches_displayed_blocks),
+    # the bicycle tracks a moving reference, so its Delta-form q_t is nonzero
+    "gamma without the A^+ Q^-1 q_{t+1} term (App. A.2)": (_gamma_drops_next_knot_term,
+                                                           lambda: KKT.test_schur_blocks_match_dense("kin_bicycle")),
+    "recovery sign (Eq. 11)": (_recovery_sign, lambda: KKT.test_pcg_and_recovery_match_direct_kkt("cartpole")),
+    "linear cost term without the Delta-form shift (Eq. 4)": (_linearise_drops_delta_form,
+                                                              SQP.test_sqp_converges_to_kkt_point_cartpole),
+    "constraint right-hand side sign (Eq. 6)": (_kkt_rhs_constraint_sign,
+                                                lambda: KKT.test_lq_kkt_matches_riccati(0.01)),
+    "merit constraint norm scaled (Algorithm 5)": (_merit_constraint_norm_doubled,
+                                                   SQP.test_line_search_penalty_formula_on_infeasible_start),
+    "RK4 stage weights": (_rk4_weights, MODELS.test_rk4_order_on_linear_system),
+    "cart-pole gravity sign (App. B.2)": (_cartpole_gravity_sign, MODELS.test_cartpole_upright_linearisation_textbook),
+    "backward without the mixed term d_theta(grad_z f^T lambda) (Eq. 3)": (_backward_drops_mixed_term,
+                                                                           VJP.test_vjp_matches_fd_lq_all_parameters),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_pin_fails_under_planted_mistake(case, monkeypatch):
+    plant, pin = CASES[case]
+    plant(monkeypatch)
+    with pytest.raises(AssertionError):
+        pin()
