@@ -13,6 +13,7 @@ from oracle import models as MD
 from oracle import ocp as O
 from oracle import schur as S
 from oracle import sqp as SQ
+from tests import test_oracle_implicit as IMPL
 from tests import test_oracle_kkt as KKT
 from tests import test_oracle_models as MODELS
 from tests import test_oracle_sqp as SQP
@@ -126,6 +127,33 @@ def _backward_drops_mixed_term(mp):
     _patch_all(mp, BW, "_phi_jets", mutant)
 
 
+def _exact_hessian_curvature_sign(mp):
+    def mutant(ocp, z, lam, b, h=None):
+        nx, nu, T = ocp.nx, ocp.nu, ocp.T
+        _, _, qd, rd, qtd = O.split_theta(ocp.one(b))
+        if h is None:
+            _, h = BW._phi_jets(ocp.one(b), z[b:b + 1])
+            bb = 0
+        else:
+            bb = b
+        L = lam[b].reshape(T + 1, nx)
+        blocks = [np.diag(np.concatenate([qd[0], rd[0]]))
+                  + np.einsum("i,ijk->jk", L[t + 1], h[bb, t][:, :nx + nu, :nx + nu]) for t in range(T)]
+        return blocks + [np.diag(qtd[0])]
+    _patch_all(mp, BW, "exact_hessian_blocks", mutant)
+
+
+def _trapezoid_one_sided(mp):
+    orig = MD.Model.residual
+
+    def mutant(self, x, u, xn, ths, thk):
+        if not self.implicit:
+            return orig(self, x, u, xn, ths, thk)
+        fa = self.fc(x, u, ths)
+        return [xn[i] - x[i] - self.dt * fa[i] for i in range(self.nx)]
+    mp.setattr(MD.Model, "residual", mutant)
+
+
 CASES = {
     "Schur off-diagonal block transposed (Eq. 10)": (_schur_offdiag_transposed,
                                                      lambda: KKT.test_schur_blocks_match_dense("lq")),
@@ -145,6 +173,9 @@ CASES = {
     "cart-pole gravity sign (App. B.2)": (_cartpole_gravity_sign, MODELS.test_cartpole_upright_linearisation_textbook),
     "backward without the mixed term d_theta(grad_z f^T lambda) (Eq. 3)": (_backward_drops_mixed_term,
                                                                            VJP.test_vjp_matches_fd_lq_all_parameters),
+    "exact Hessian with the curvature sign flipped (Sec. 3.4)": (_exact_hessian_curvature_sign,
+                                                                 VJP.test_vjp_exact_hessian_matches_fd_cartpole),
+    "trapezoidal residual with one endpoint only": (_trapezoid_one_sided, IMPL.test_trapezoid_rule_is_second_order),
 }
 
 
