@@ -154,6 +154,64 @@ def _trapezoid_one_sided(mp):
     mp.setattr(MD.Model, "residual", mutant)
 
 
+def _pcg_beta_inverted(mp):
+    def mutant(D, Off, Pd, Po, gamma, lam0, rel_tol, max_iter):
+        mv = S.block_tridiag_matvec
+        lam = lam0.copy()
+        r = gamma - mv(D, Off, lam)
+        rt = mv(Pd, Po, r)
+        p = rt.copy()
+        eta = np.einsum("bti,bti->b", r, rt)
+        eta0 = np.einsum("bti,bti->b", gamma, mv(Pd, Po, gamma))
+        iters = np.zeros(lam.shape[0], dtype=np.int64)
+        for _ in range(max_iter):
+            y = mv(D, Off, p)
+            alpha = eta / np.einsum("bti,bti->b", p, y)
+            lam += alpha[:, None, None] * p
+            r -= alpha[:, None, None] * y
+            rt = mv(Pd, Po, r)
+            eta_new = np.einsum("bti,bti->b", r, rt)
+            p = rt + (eta / eta_new)[:, None, None] * p      # planted: beta inverted
+            eta = eta_new
+            iters += 1
+            if (eta <= rel_tol * eta0).all():
+                break
+        return lam, iters, eta, eta0
+    _patch_all(mp, S, "pcg", mutant)
+
+
+def _preconditioner_diagonal_not_inverted(mp):
+    orig = S.preconditioner_blocks
+
+    def mutant(D, Off):
+        _, P = orig(D, Off)
+        return D.copy(), P
+    _patch_all(mp, S, "preconditioner_blocks", mutant)
+
+
+def _fiala_cubic_sign(mp):
+    def mutant(alpha, mu, c_alpha, fz):
+        t = MD.tan(alpha)
+        sat = 3.0 * mu * fz / c_alpha
+        lin = (-1.0 * c_alpha * t + (c_alpha * c_alpha / (3.0 * mu * fz)) * MD.absval(t) * t
+               + (c_alpha * c_alpha * c_alpha / (27.0 * mu * mu * fz * fz)) * t * t * t)  # planted sign
+        slide = -1.0 * mu * fz * np.sign(MD.value(t))
+        return MD.where(np.abs(MD.value(t)) < np.abs(MD.value(sat)), lin, slide)
+    _patch_all(mp, MD, "fiala_lateral_force", mutant)
+
+
+def _rigid_body_gyroscopic_sign(mp):
+    orig = MD.RigidBody12.fc
+
+    def mutant(self, x, u, ths):
+        out = list(orig(self, x, u, ths))
+        wx, wy, wz = x[9:12]
+        m, jx, jy, jz = ths
+        out[9] = out[9] + 2.0 * (wy * (jz * wz) - wz * (jy * wy)) / jx   # w x (J w) sign flipped in x
+        return out
+    mp.setattr(MD.RigidBody12, "fc", mutant)
+
+
 CASES = {
     "Schur off-diagonal block transposed (Eq. 10)": (_schur_offdiag_transposed,
                                                      lambda: KKT.test_schur_blocks_match_dense("lq")),
@@ -176,6 +234,12 @@ CASES = {
     "exact Hessian with the curvature sign flipped (Sec. 3.4)": (_exact_hessian_curvature_sign,
                                                                  VJP.test_vjp_exact_hessian_matches_fd_cartpole),
     "trapezoidal residual with one endpoint only": (_trapezoid_one_sided, IMPL.test_trapezoid_rule_is_second_order),
+    "PCG beta inverted (Algorithm 4)": (_pcg_beta_inverted, lambda: KKT.test_pcg_and_recovery_match_direct_kkt("lq")),
+    "preconditioner diagonal blocks not inverted (Eq. 10)": (_preconditioner_diagonal_not_inverted,
+                                                             KKT.test_preconditioner_matches_displayed_blocks),
+    "Fiala cubic term sign": (_fiala_cubic_sign, MODELS.test_fiala_curve_properties),
+    "rigid-body gyroscopic term sign": (_rigid_body_gyroscopic_sign,
+                                        lambda: MODELS.test_rigid_body_rotational_energy_conserved(MD.RigidBody12)),
 }
 
 
