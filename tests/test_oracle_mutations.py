@@ -13,6 +13,7 @@ from oracle import models as MD
 from oracle import ocp as O
 from oracle import schur as S
 from oracle import sqp as SQ
+from tests import test_oracle_cost as COST
 from tests import test_oracle_implicit as IMPL
 from tests import test_oracle_kkt as KKT
 from tests import test_oracle_models as MODELS
@@ -212,6 +213,27 @@ def _rigid_body_gyroscopic_sign(mp):
     mp.setattr(MD.RigidBody12, "fc", mutant)
 
 
+def _cost_gradient_without_reference(mp):
+    def mutant(ocp, z):
+        _, _, qd, rd, qtd = O.split_theta(ocp)
+        x, u = O.split_z(ocp, z)
+        gx = x * qd[:, None, :]            # planted: x_ref left out
+        gx[:, -1] = x[:, -1] * qtd
+        return O.join_z(gx, u * rd[:, None, :])
+    _patch_all(mp, O, "cost_gradient", mutant)
+
+
+def _cost_value_terminal_factor(mp):
+    orig = O.cost_value
+
+    def mutant(ocp, z):
+        _, _, _, _, qtd = O.split_theta(ocp)
+        x, _ = O.split_z(ocp, z)
+        dT = x[:, -1] - ocp.x_ref[:, -1]
+        return orig(ocp, z) + 0.5 * np.einsum("bn,bn->b", dT ** 2, qtd)   # planted: no 1/2 at t = T
+    _patch_all(mp, O, "cost_value", mutant)
+
+
 CASES = {
     "Schur off-diagonal block transposed (Eq. 10)": (_schur_offdiag_transposed,
                                                      lambda: KKT.test_schur_blocks_match_dense("lq")),
@@ -240,6 +262,9 @@ CASES = {
     "Fiala cubic term sign": (_fiala_cubic_sign, MODELS.test_fiala_curve_properties),
     "rigid-body gyroscopic term sign": (_rigid_body_gyroscopic_sign,
                                         lambda: MODELS.test_rigid_body_rotational_energy_conserved(MD.RigidBody12)),
+    "cost gradient without the reference": (_cost_gradient_without_reference,
+                                            COST.test_cost_gradient_matches_differences_with_reference),
+    "terminal cost without its 1/2": (_cost_value_terminal_factor, COST.test_cost_value_hand_computed),
 }
 
 
