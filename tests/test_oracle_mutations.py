@@ -234,6 +234,48 @@ def _cost_value_terminal_factor(mp):
     _patch_all(mp, O, "cost_value", mutant)
 
 
+def _lq_transition_transposed(mp):
+    def mutant(self, x, u, ths, thk):
+        nx, nu = self.nx, self.nu
+        out = []
+        for i in range(nx):
+            acc = thk[nx * nx + nx * nu + i]
+            for j in range(nx):
+                acc = acc + thk[j * nx + i] * x[j]          # planted: Abar^T
+            for j in range(nu):
+                acc = acc + thk[nx * nx + i * nu + j] * u[j]
+            out.append(acc)
+        return out
+    mp.setattr(MD.LQ, "step", mutant)
+
+
+def _pendulum_gravity_sign(mp):
+    def mutant(self, x, u, ths):
+        phi, w = x
+        m, L = ths
+        return [w, -(MD.GRAVITY / L) * MD.sin(phi) + u[0] / (m * L * L)]
+    mp.setattr(MD.Pendulum, "fc", mutant)
+
+
+def _bicycle_sin_for_tan(mp):
+    def mutant(self, x, u, ths):
+        px, py, psi, v = x
+        delta, a = u
+        (lwb,) = ths
+        return [v * MD.cos(psi), v * MD.sin(psi), v * MD.sin(delta) / lwb, a]
+    mp.setattr(MD.KinematicBicycle, "fc", mutant)
+
+
+def _banded_solve_swapped_entries(mp):
+    orig = O.solve_kkt_banded
+
+    def mutant(trip, rhs, nx, nu, T):
+        sol = orig(trip, rhs, nx, nu, T).copy()
+        sol[[0, 1]] = sol[[1, 0]]                        # planted: two unknowns swapped
+        return sol
+    _patch_all(mp, O, "solve_kkt_banded", mutant)
+
+
 CASES = {
     "Schur off-diagonal block transposed (Eq. 10)": (_schur_offdiag_transposed,
                                                      lambda: KKT.test_schur_blocks_match_dense("lq")),
@@ -265,6 +307,12 @@ CASES = {
     "cost gradient without the reference": (_cost_gradient_without_reference,
                                             COST.test_cost_gradient_matches_differences_with_reference),
     "terminal cost without its 1/2": (_cost_value_terminal_factor, COST.test_cost_value_hand_computed),
+    "LQ transition matrix transposed (App. B.1)": (_lq_transition_transposed,
+                                                  lambda: KKT.test_lq_kkt_matches_riccati(0.0)),
+    "pendulum gravity sign": (_pendulum_gravity_sign, MODELS.test_pendulum_conserves_energy_unforced),
+    "bicycle yaw rate with sin(delta) for tan(delta)": (_bicycle_sin_for_tan, MODELS.test_kinematic_bicycle_circle),
+    "banded KKT solve with two unknowns swapped": (_banded_solve_swapped_entries,
+                                                   lambda: KKT.test_banded_solve_matches_dense_lu("cartpole")),
 }
 
 
