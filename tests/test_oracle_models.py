@@ -229,3 +229,42 @@ def test_rk4_order_on_linear_system():
         series = 1 + a * dt + (a * dt) ** 2 / 2 + (a * dt) ** 3 / 6 + (a * dt) ** 4 / 24
         assert abs(out - series) < 1e-15
         assert abs(out - np.exp(a * dt)) < (abs(a) * dt) ** 5 / 100
+
+
+def test_single_track_linear_lateral_dynamics_textbook():
+    """Straight running (Vy = r = delta = 0, Vx = V): the Jacobian of the lateral states is the
+    textbook linear single-track model with axle cornering stiffness C (the Fiala slope at zero
+    slip): dr'/d(Vy, r, delta) = (-C (a - b)/(V Iz), -C (a^2 + b^2)/(V Iz), C a / Iz),
+    dVy'/d(Vy, r, delta) = (-2C/(m V), -C (a - b)/(m V) - V, C / m)."""
+    model = SingleTrackFiala(0.02)
+    V, C, mu = 12.0, 8e4, 0.9
+    a, b, m, Iz = model.a, model.b, model.m, model.Iz
+    k = 8
+    vals = [0.0, 0.0, 0.3, 0.0, 0.0, V]
+    xs = [Jet.seed(np.array([vals[i]]), i, k) for i in range(6)]
+    us = [Jet.seed(np.array([0.0]), 6, k), Jet.seed(np.array([0.0]), 7, k)]
+    f = model.fc(xs, us, [mu, C])
+    d_r = f[3].g[0][[4, 3, 6]]
+    d_vy = f[4].g[0][[4, 3, 6]]
+    np.testing.assert_allclose(d_r, [-C * (a - b) / (V * Iz), -C * (a * a + b * b) / (V * Iz), C * a / Iz],
+                               rtol=1e-12)
+    np.testing.assert_allclose(d_vy, [-2 * C / (m * V), -C * (a - b) / (m * V) - V, C / m], rtol=1e-12)
+
+
+@pytest.mark.parametrize("cls", [RigidBody12, Attitude])
+def test_body_rates_respond_to_torque_at_rest(cls):
+    """At zero body rates (and level attitude) the Euler equations reduce to w' = tau / J."""
+    model = cls(0.05)
+    rng = np.random.default_rng(4)
+    tau = rng.standard_normal(3)
+    if cls is RigidBody12:
+        th = [1.2, 0.01, 0.02, 0.03]
+        J = np.array(th[1:])
+        f = model.fc([np.zeros(1)] * 12, [np.zeros(1)] + [np.array([t]) for t in tau], [np.array([v]) for v in th])
+        wdot = np.array([np.broadcast_to(fi, (1,))[0] for fi in f[9:12]])
+    else:
+        th = [0.5, 0.7, 0.9]
+        J = np.array(th)
+        f = model.fc([np.zeros(1)] * 3, [np.array([t]) for t in tau], [np.array([v]) for v in th])
+        wdot = np.array([np.broadcast_to(fi, (1,))[0] for fi in f])
+    np.testing.assert_allclose(wdot, tau / J, rtol=1e-14)

@@ -276,6 +276,33 @@ def _banded_solve_swapped_entries(mp):
     _patch_all(mp, O, "solve_kkt_banded", mutant)
 
 
+def _single_track_axles_swapped(mp):
+    orig = MD.SingleTrackFiala.fc
+
+    def mutant(self, x, u, ths):
+        out = list(orig(self, x, u, ths))
+        px, py, psi, r, vy, vx = x
+        delta, fx = u
+        mu, ca = ths
+        a, b, m = self.a, self.b, self.m
+        fyf = MD.fiala_lateral_force(MD.atan((vy + a * r) / vx) - delta, mu, ca, m * MD.GRAVITY * b / (a + b))
+        fyr = MD.fiala_lateral_force(MD.atan((vy - b * r) / vx), mu, ca, m * MD.GRAVITY * a / (a + b))
+        out[3] = (b * fyf * MD.cos(delta) - a * fyr) / self.Iz       # planted: lever arms swapped
+        return out
+    mp.setattr(MD.SingleTrackFiala, "fc", mutant)
+
+
+def _attitude_torque_inertia(mp):
+    orig = MD.Attitude.fc
+
+    def mutant(self, x, u, ths):
+        out = list(orig(self, x, u, ths))
+        j1, j2, j3 = ths
+        out[0] = out[0] - u[0] / j1 + u[0] / j2                        # planted: tau_1 / J_2
+        return out
+    mp.setattr(MD.Attitude, "fc", mutant)
+
+
 CASES = {
     "Schur off-diagonal block transposed (Eq. 10)": (_schur_offdiag_transposed,
                                                      lambda: KKT.test_schur_blocks_match_dense("lq")),
@@ -313,6 +340,10 @@ CASES = {
     "bicycle yaw rate with sin(delta) for tan(delta)": (_bicycle_sin_for_tan, MODELS.test_kinematic_bicycle_circle),
     "banded KKT solve with two unknowns swapped": (_banded_solve_swapped_entries,
                                                    lambda: KKT.test_banded_solve_matches_dense_lu("cartpole")),
+    "single-track lever arms swapped in the yaw equation": (_single_track_axles_swapped,
+                                                            MODELS.test_single_track_linear_lateral_dynamics_textbook),
+    "attitude torque divided by the wrong inertia (App. B.1)": (
+        _attitude_torque_inertia, lambda: MODELS.test_body_rates_respond_to_torque_at_rest(MD.Attitude)),
 }
 
 
