@@ -268,3 +268,34 @@ def test_body_rates_respond_to_torque_at_rest(cls):
         f = model.fc([np.zeros(1)] * 3, [np.array([t]) for t in tau], [np.array([v]) for v in th])
         wdot = np.array([np.broadcast_to(fi, (1,))[0] for fi in f])
     np.testing.assert_allclose(wdot, tau / J, rtol=1e-14)
+
+
+def _rot_zyx(ro, pi, ya):
+    """Textbook ZYX rotation body -> world: Rz(yaw) Ry(pitch) Rx(roll)."""
+    cr, sr, cp, sp, cy, sy = np.cos(ro), np.sin(ro), np.cos(pi), np.sin(pi), np.cos(ya), np.sin(ya)
+    Rz = np.array([[cy, -sy, 0], [sy, cy, 0], [0, 0, 1]])
+    Ry = np.array([[cp, 0, sp], [0, 1, 0], [-sp, 0, cp]])
+    Rx = np.array([[1, 0, 0], [0, cr, -sr], [0, sr, cr]])
+    return Rz @ Ry @ Rx
+
+
+def test_rigid_body_kinematics_match_rotation_matrix():
+    """Thrust acts along the body z axis, R e3, and the Euler-angle rates reproduce the body
+    rates: dR/dt (along the oracle's angle rates) = R [w]x."""
+    model = RigidBody12(0.02)
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        ang = rng.uniform(-0.6, 0.6, 3)
+        w = rng.standard_normal(3)
+        dT = rng.uniform(-2.0, 2.0)
+        th = [1.3, 0.011, 0.013, 0.021]
+        x = [np.array([v]) for v in np.concatenate([np.zeros(6), ang, w])]
+        u = [np.array([dT]), np.zeros(1), np.zeros(1), np.zeros(1)]
+        f = np.array([np.broadcast_to(fi, (1,))[0] for fi in model.fc(x, u, [np.array([v]) for v in th])])
+        R = _rot_zyx(*ang)
+        acc = (th[0] * GRAVITY + dT) / th[0]
+        np.testing.assert_allclose(f[3:6] + [0.0, 0.0, GRAVITY], acc * R[:, 2], rtol=1e-12, atol=1e-12)
+        h = 1e-6
+        dR = (_rot_zyx(*(ang + h * f[6:9])) - _rot_zyx(*(ang - h * f[6:9]))) / (2 * h)
+        W = np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]])
+        np.testing.assert_allclose(dR, R @ W, atol=1e-8)

@@ -303,6 +303,18 @@ def _attitude_torque_inertia(mp):
     mp.setattr(MD.Attitude, "fc", mutant)
 
 
+def _rigid_body_euler_rate_sign(mp):
+    orig = MD.RigidBody12.fc
+
+    def mutant(self, x, u, ths):
+        out = list(orig(self, x, u, ths))
+        ro, pi = x[6], x[7]
+        wy = x[10]
+        out[6] = out[6] - 2.0 * MD.sin(ro) * (MD.sin(pi) / MD.cos(pi)) * wy     # planted: sign of a roll-rate term
+        return out
+    mp.setattr(MD.RigidBody12, "fc", mutant)
+
+
 CASES = {
     "Schur off-diagonal block transposed (Eq. 10)": (_schur_offdiag_transposed,
                                                      lambda: KKT.test_schur_blocks_match_dense("lq")),
@@ -344,6 +356,8 @@ CASES = {
                                                             MODELS.test_single_track_linear_lateral_dynamics_textbook),
     "attitude torque divided by the wrong inertia (App. B.1)": (
         _attitude_torque_inertia, lambda: MODELS.test_body_rates_respond_to_torque_at_rest(MD.Attitude)),
+    "rigid-body Euler-rate term sign": (_rigid_body_euler_rate_sign,
+                                        MODELS.test_rigid_body_kinematics_match_rotation_matrix),
 }
 
 
