@@ -315,6 +315,27 @@ def _rigid_body_euler_rate_sign(mp):
     mp.setattr(MD.RigidBody12, "fc", mutant)
 
 
+def _line_search_eta(mp):
+    orig = SQ.line_search
+
+    def mutant(ocp, z, z_plus, alphas=SQ.LS_ALPHAS, eta=SQ.LS_ETA):
+        return orig(ocp, z, z_plus, alphas, 0.5)                     # planted: eta = 0.5
+    _patch_all(mp, SQ, "line_search", mutant)
+
+
+def _line_search_takes_last_passing_step(mp):
+    orig = SQ.line_search
+
+    def mutant(ocp, z, z_plus, alphas=SQ.LS_ALPHAS, eta=SQ.LS_ETA):
+        alpha, diag = orig(ocp, z, z_plus, alphas, eta)
+        for b in range(ocp.B):
+            ok = np.where(diag["delta"][b] < 0.0)[0]
+            if ok.size:
+                alpha[b] = alphas[ok[-1]]                             # planted: last passing alpha
+        return alpha, diag
+    _patch_all(mp, SQ, "line_search", mutant)
+
+
 CASES = {
     "Schur off-diagonal block transposed (Eq. 10)": (_schur_offdiag_transposed,
                                                      lambda: KKT.test_schur_blocks_match_dense("lq")),
@@ -358,6 +379,10 @@ CASES = {
         _attitude_torque_inertia, lambda: MODELS.test_body_rates_respond_to_torque_at_rest(MD.Attitude)),
     "rigid-body Euler-rate term sign": (_rigid_body_euler_rate_sign,
                                         MODELS.test_rigid_body_kinematics_match_rotation_matrix),
+    "decrease-test constant 0.5 for 0.4 (Algorithm 5)": (_line_search_eta,
+                                                         SQP.test_line_search_closed_form_on_feasible_lq),
+    "line search keeps the last passing step (Algorithm 5)": (_line_search_takes_last_passing_step,
+                                                              SQP.test_line_search_closed_form_on_feasible_lq),
 }
 
 
