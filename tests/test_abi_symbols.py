@@ -50,3 +50,18 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu():
     assert lib.dmpc_create_problem_batch(None, 1, None, None, ctypes.byref(h)) == 1
     assert h.value is None
     assert lib.dmpc_vjp(None, None, None, None, None, None, None) == 1
+
+
+def test_product_path_fails_loudly_without_the_library():
+    """No CPU fallback: with the CUDA library absent, creating a batch raises at once."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("from paper_2510_06179_gb300.solver import OCPBatch\n"
+            "OCPBatch(('cartpole', 4, 1, 10, 0.05), batch=2, device='cpu')\n")
+    env = dict(os.environ, DMPC_LIB=os.path.join(root, "_no_such_dir", "libdmpc.so"))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode != 0
+    assert "CUDA library not built" in r.stderr
