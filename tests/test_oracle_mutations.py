@@ -336,6 +336,20 @@ def _line_search_takes_last_passing_step(mp):
     _patch_all(mp, SQ, "line_search", mutant)
 
 
+def _dF_dtheta_cost_rows_without_reference(mp):
+    orig = BW.dF_dtheta
+
+    def mutant(ocp, z, lam, b, g=None, h=None):
+        M = orig(ocp, z, lam, b, g, h)
+        nx, nu, T = ocp.nx, ocp.nu, ocp.T
+        _, _, o_q, _, o_qt, _ = O.theta_offsets(ocp.model, T)
+        for t in range(T):
+            M[O.x_index(nx, nu, t), o_q + np.arange(nx)] += ocp.x_ref[b, t]    # planted: x for x - x_ref
+        M[O.x_index(nx, nu, T), o_qt + np.arange(nx)] += ocp.x_ref[b, T]
+        return M
+    _patch_all(mp, BW, "dF_dtheta", mutant)
+
+
 CASES = {
     "Schur off-diagonal block transposed (Eq. 10)": (_schur_offdiag_transposed,
                                                      lambda: KKT.test_schur_blocks_match_dense("lq")),
@@ -383,6 +397,8 @@ CASES = {
                                                          SQP.test_line_search_closed_form_on_feasible_lq),
     "line search keeps the last passing step (Algorithm 5)": (_line_search_takes_last_passing_step,
                                                               SQP.test_line_search_closed_form_on_feasible_lq),
+    "dF/dtheta cost-weight columns without the reference (Eq. 3)": (
+        _dF_dtheta_cost_rows_without_reference, lambda: VJP.test_dF_dtheta_matches_differenced_residual("kin_bicycle")),
 }
 
 

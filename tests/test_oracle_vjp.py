@@ -3,6 +3,7 @@ differences of the loss: exact for affine dynamics (LQ) with the Gauss-Newton KK
 and exact on nonlinear dynamics with the exact-Hessian KKT matrix; the Gauss-Newton gap on
 nonlinear dynamics (Sec. 3.4) is measured, not gated."""
 import numpy as np
+import pytest
 
 from paper_2510_06179_gb300 import workloads
 from oracle import ocp as O
@@ -72,10 +73,13 @@ def test_vjp_gn_equals_exact_for_affine_dynamics():
     np.testing.assert_allclose(a["dtheta"], b["dtheta"], rtol=1e-10, atol=1e-12)
 
 
-def test_dF_dtheta_matches_differenced_residual():
-    """dF/dtheta (assembled from jets) vs central differences of F(z, lambda, theta) (Eq. 1)."""
+@pytest.mark.parametrize("name", ["cartpole", "kin_bicycle"])
+def test_dF_dtheta_matches_differenced_residual(name):
+    """dF/dtheta (assembled from jets) vs central differences of F(z, lambda, theta) (Eq. 1);
+    the bicycle tracks a nonzero reference, which enters the cost-weight columns."""
     from oracle.backward import dF_dtheta
-    w = workloads.cartpole_config(B=1, T=5, seed=9)
+    w = (workloads.cartpole_config(B=1, T=5, seed=9) if name == "cartpole"
+         else workloads.bicycle_config(B=1, T=5, seed=9))
     ocp = to_ocp(w)
     rng = np.random.default_rng(4)
     z = 0.5 * rng.standard_normal((1, ocp.n))
