@@ -183,6 +183,7 @@ def accuracy(z, dtheta, alpha, ref, tie=1e-5):
             "z_rel_err_max_agree": f(ez[agree]), "dtheta_rel_err_max_agree": f(eg[agree]),
             "agree_within_gates": int(((ez <= 1e-4) & (eg <= 1e-3) & agree).sum()),
             "branched_near_tie": int(near_tie.sum()), "branched_other": int((~agree & ~near_tie).sum()),
+            "branched_z_within_1e-4": int(((ez <= 1e-4) & ~agree).sum()),
             "z_within_1e-4_all": int((ez <= 1e-4).sum()), "dtheta_within_1e-3_all": int((eg <= 1e-3).sum()),
             "z_rel_err_median": float(np.median(ez))}
 

@@ -39,6 +39,7 @@ def test_branch_classification_and_gates():
     assert acc["agree_within_gates"] == 1
     assert abs(acc["z_rel_err_max_agree"] - 1e-3) < 1e-9
     assert acc["z_within_1e-4_all"] == 3
+    assert acc["branched_z_within_1e-4"] == 2     # OCPs 1 and 2 branched but kept their solutions
 
 
 def test_serving_class_priorities_order_by_cost():
