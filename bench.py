@@ -82,12 +82,31 @@ def throughput(world, steps, seconds):
 # ---------------------------------------------------------------------- DRAM traffic
 # dram__bytes_read.sum + dram__bytes_write.sum of one forward launch from an ncu capture of this
 # bench step (the command and counters are summarised under profiles/), with the hash of the
-# kernel sources it was taken on; reported only while the sources still hash the same.
-TRAFFIC_CAPTURE = {"src_sha256_16": "354447caefe88efa", "bytes_per_launch": 625664 + 150528}
+# kernel sources it was taken on; reported only while the sources still hash the same.  The hash
+# ignores comments and whitespace, so only an edit of the code itself invalidates a capture.
+TRAFFIC_CAPTURE = {"src_sha256_16": "c82ffdbbaa856498", "bytes_per_launch": 625664 + 150528}
+
+
+def _code_tokens(text):
+    """C/C++/CUDA source with comments removed and whitespace runs collapsed (string and
+    character literals kept as they are)."""
+    import re
+    pat = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\])*"|\'(?:\\.|[^\'\\])*\'|\s+|[^\s"\'/]+|/', re.S)
+    out = []
+    for m in pat.finditer(text):
+        t = m.group(0)
+        if t.startswith("//") or t.startswith("/*"):
+            out.append(" ")
+        elif t.isspace():
+            out.append(" ")
+        else:
+            out.append(t)
+    return " ".join("".join(out).split())
 
 
 def kernel_source_hash():
-    """First 16 hex digits of a SHA-256 over the CUDA sources and the C-ABI header."""
+    """First 16 hex digits of a SHA-256 over the code of the CUDA sources and the C-ABI header
+    (comments and whitespace removed)."""
     import glob
     import hashlib
     root = os.path.dirname(os.path.abspath(__file__))
@@ -97,8 +116,8 @@ def kernel_source_hash():
     h = hashlib.sha256()
     for f in files:
         h.update(f.encode())
-        with open(os.path.join(root, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(root, f), encoding="utf-8") as fh:
+            h.update(_code_tokens(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

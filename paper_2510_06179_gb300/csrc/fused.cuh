@@ -1343,10 +1343,10 @@ __device__ __forceinline__ void reg_row(const float (&Md)[NX * NX], const float 
   }
 }
 
-// a4, register-resident variant (one knot per lane, K <= TEAM, nx <= 4): the same algorithm
+// a4, register-resident variant (one knot per lane, K <= TEAM, nx <= 6): the same algorithm
 // as stage_pcg (FP32 iteration, FP64 solution with reliable updates, double-float rescue), with the
-// S and Phi^-1 blocks of the lane's knot held in registers for the whole solve and the
-// neighbour coupling done with shuffles, so the inner loop touches no memory.
+// S and Phi^-1 blocks of the lane's knot held in registers for the whole solve and the neighbour
+// coupling done with shuffles (a small shared buffer across warps), so the loop reads no blocks.
 template <class M, int TEAM>
 __device__ __noinline__ int stage_pcg_reg(Ctx<M, TEAM>& c) {
   constexpr int NX = M::NX;
@@ -1924,7 +1924,7 @@ __device__ __noinline__ int stage_pcg_warp(Ctx<M, 32>& c) {
   return it;
 }
 
-// PCG entry: the register-resident inner loop when one knot per lane fits (nx <= 4).
+// PCG entry: the register-resident inner loop when one knot per lane fits (nx <= 6).
 template <class M, int TEAM>
 __device__ __forceinline__ int run_pcg(Ctx<M, TEAM>& c) {
   if constexpr (M::NX <= 4) {
