@@ -76,3 +76,13 @@ def test_reference_arm_prints_one_contract_line():
     cfg = d["config"]
     assert cfg["workload"] == bench.WORKLOAD and cfg["batch_per_gpu"] == bench.B and cfg["T"] == bench.T
     assert cfg["sqp_iters"] == bench.SQP_ITERS and cfg["ocps_per_step"] == 2
+
+
+def test_code_hash_ignores_comments_and_whitespace_only():
+    a = 'int f(int x) {  // twice\n  return 2 * x; /* doubled */ }\nconst char* s = "a // b";'
+    b = 'int f(int x) {\n\n  return 2 * x;  }  // no comment here\nconst char* s = "a // b";'
+    c = 'int f(int x) { return 3 * x; }\nconst char* s = "a // b";'
+    assert bench._code_tokens(a) == bench._code_tokens(b)
+    assert bench._code_tokens(a) != bench._code_tokens(c)
+    assert '"a // b"' in bench._code_tokens(a)
+    assert len(bench.kernel_source_hash()) == 16
