@@ -208,10 +208,13 @@ class DiffMPCFunction(torch.autograd.Function):
 
     The OCPBatch keeps the latest solution resident on the device.  When the same batch solved
     again after this call (several solves in one graph, e.g. a closed-loop rollout), backward
-    first restores this call's solution and inputs with set_solution."""
+    first restores this call's solution and inputs with set_solution.  Gradients flow to x_s and
+    theta only: x_ref must not require a gradient, and z_init is a starting point of the solve."""
 
     @staticmethod
     def forward(ctx, x_s, theta, batch, x_ref=None, z_init=None):
+        if x_ref is not None and x_ref.requires_grad:
+            raise ValueError("no gradient with respect to x_ref is computed; pass x_ref.detach()")
         xs_d, th_d = x_s.detach().contiguous(), theta.detach().contiguous()
         xr_d = None if x_ref is None else x_ref.detach().contiguous()
         out = batch.solve(xs_d, th_d, xr_d, z_init, want_stats=False)

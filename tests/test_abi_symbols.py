@@ -65,3 +65,16 @@ def test_product_path_fails_loudly_without_the_library():
                        timeout=300)
     assert r.returncode != 0
     assert "CUDA library not built" in r.stderr
+
+
+def test_reference_requiring_grad_is_rejected():
+    """The backward returns gradients for x_s and theta only, so a reference that asks for one
+    is refused before any solve (checked without a GPU: the batch is never touched)."""
+    import pytest
+    import torch
+    from paper_2510_06179_gb300.solver import DiffMPCFunction
+    x_s = torch.zeros(4)
+    theta = torch.zeros(7, requires_grad=True)
+    x_ref = torch.zeros(8, requires_grad=True)
+    with pytest.raises(ValueError, match="x_ref"):
+        DiffMPCFunction.apply(x_s, theta, object(), x_ref, None)
