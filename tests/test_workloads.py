@@ -62,3 +62,30 @@ def test_serving_trace_poisson_and_horizons():
     assert Ts.min() >= 16 and Ts.max() <= 256
     assert np.median(Ts) < 0.6 * 256                                           # log-uniform, not uniform
     assert {r["nx"] for r in tr} == {2, 4, 6, 12}
+
+
+def test_vehicle_recipe_and_reference_path():
+    w = workloads.vehicle_config(B=512, T=50, seed=2)
+    mu, ca = w.theta[:, 0], w.theta[:, 1]
+    assert 0.3 <= mu.min() and mu.max() <= 1.1 and 5e4 <= ca.min() and ca.max() <= 1.5e5
+    ref = w.x_ref.astype(np.float64)
+    V = ref[:, 0, 5]
+    assert 8.0 <= V.min() and V.max() <= 15.0 and np.all(ref[:, :, 5] == ref[:, :1, 5])   # constant speed
+    assert not ref[:, :, 4].any()                                                          # Vy = 0
+    # the path is driven at speed V: consecutive reference points are about V dt apart
+    step = np.hypot(np.diff(ref[:, :, 0], axis=1), np.diff(ref[:, :, 1], axis=1))
+    np.testing.assert_allclose(step, np.broadcast_to(V[:, None] * w.dt, step.shape), rtol=1e-4)
+    # yaw rate = V kappa with |kappa| <= 0.05
+    assert np.abs(ref[:, :, 3] / V[:, None]).max() <= 0.05 + 1e-6
+    assert w.extra["features"].shape == (512, 16)
+
+
+def test_rigid_body_and_attitude_recipes():
+    rb = workloads.rigid_body_config(B=256, T=8, seed=3)
+    m, J = rb.theta[:, 0], rb.theta[:, 1:4]
+    assert 0.5 <= m.min() and m.max() <= 1.5 and 0.005 <= J.min() and J.max() <= 0.02
+    assert np.abs(rb.x_s[:, 6:9]).max() <= 0.3 and not rb.x_ref.any()
+    at = workloads.attitude_config(B=256, seed=3)
+    assert at.T == 25 and abs(at.dt - 0.1) < 1e-12
+    assert 0.1 <= at.theta[:, :3].min() and at.theta[:, :3].max() <= 10.0
+    assert np.abs(at.x_s).max() <= 1.0
