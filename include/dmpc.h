@@ -177,7 +177,9 @@ dmpc_err dmpc_vjp_plain(dmpc_handle* h, const float* dl_dz, float* dl_dtheta, fl
  *     iterate.  Shapes must fit the slot (n, m, p, x_ref length and workspace) else
  *     DMPC_E_BUDGET; a single-model handle keeps its model.  Ordered on the handle's stream.
  *   dmpc_solve_subset: run opt.sqp_iters SQP iterations (Algorithm 2) on the slots listed in the
- *     DEVICE array index[0..n-1], each continuing from its resident iterate (or cold when reset);
+ *     DEVICE array index[0..n-1] (distinct slot numbers in [0, batch): the kernel reads them as
+ *     given, so the caller guarantees this), each continuing from its resident iterate (or cold
+ *     when reset);
  *     arrays are the handle-wide packed arrays of dmpc_layout (only listed slots are read or
  *     written).  With sqp_iters = 1 every call advances each listed problem by one SQP
  *     iteration, so requests can join between calls (continuous batching).
