@@ -350,6 +350,17 @@ def _dF_dtheta_cost_rows_without_reference(mp):
     _patch_all(mp, BW, "dF_dtheta", mutant)
 
 
+def _implicit_a_plus_transposed(mp):
+    orig = O.linearise
+
+    def mutant(ocp, z):
+        qp = orig(ocp, z)
+        if not ocp.model.implicit:
+            return qp
+        return dataclasses.replace(qp, Ap=np.swapaxes(qp.Ap, -1, -2))   # planted: A^+ transposed
+    _patch_all(mp, O, "linearise", mutant)
+
+
 CASES = {
     "Schur off-diagonal block transposed (Eq. 10)": (_schur_offdiag_transposed,
                                                      lambda: KKT.test_schur_blocks_match_dense("lq")),
@@ -399,6 +410,9 @@ CASES = {
                                                               SQP.test_line_search_closed_form_on_feasible_lq),
     "dF/dtheta cost-weight columns without the reference (Eq. 3)": (
         _dF_dtheta_cost_rows_without_reference, lambda: VJP.test_dF_dtheta_matches_differenced_residual("kin_bicycle")),
+    "implicit integrator's A^+ transposed (Eq. 4)": (
+        _implicit_a_plus_transposed,
+        lambda: IMPL.test_implicit_linearisation_matches_differences(IMPL.workloads.cartpole_config)),
 }
 
 
