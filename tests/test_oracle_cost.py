@@ -50,3 +50,12 @@ def test_cost_gradient_matches_differences_with_reference():
         zm[:, i] -= h
         fd[:, i] = (O.cost_value(ocp, zp) - O.cost_value(ocp, zm)) / (2 * h)
     np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-6 * np.abs(fd).max())
+
+
+def test_pd_projection_reading():
+    """Reading of the PD projection (Sec. 3.1): each diagonal entry is clamped below at
+    1e-6 max(1, largest entry); positive entries above the floor are left alone."""
+    d = np.array([[-1.0, 0.0, 2e-7, 5.0], [0.5, -2.0, 0.25, 1e-3]])
+    out = O.pd_project_diag(d)
+    np.testing.assert_allclose(out[0], [5e-6, 5e-6, 5e-6, 5.0], rtol=1e-14)
+    np.testing.assert_allclose(out[1], [0.5, 1e-6, 0.25, 1e-3], rtol=1e-14)

@@ -361,6 +361,12 @@ def _implicit_a_plus_transposed(mp):
     _patch_all(mp, O, "linearise", mutant)
 
 
+def _pd_floor_without_unit_bound(mp):
+    def mutant(d):
+        return np.maximum(d, O.PD_EPS * d.max(axis=-1, keepdims=True))   # planted: no max(1, .)
+    _patch_all(mp, O, "pd_project_diag", mutant)
+
+
 CASES = {
     "Schur off-diagonal block transposed (Eq. 10)": (_schur_offdiag_transposed,
                                                      lambda: KKT.test_schur_blocks_match_dense("lq")),
@@ -392,6 +398,8 @@ CASES = {
     "cost gradient without the reference": (_cost_gradient_without_reference,
                                             COST.test_cost_gradient_matches_differences_with_reference),
     "terminal cost without its 1/2": (_cost_value_terminal_factor, COST.test_cost_value_hand_computed),
+    "PD-projection floor without its unit bound (Sec. 3.1)": (_pd_floor_without_unit_bound,
+                                                              COST.test_pd_projection_reading),
     "LQ transition matrix transposed (App. B.1)": (_lq_transition_transposed,
                                                   lambda: KKT.test_lq_kkt_matches_riccati(0.0)),
     "pendulum gravity sign": (_pendulum_gravity_sign, MODELS.test_pendulum_conserves_energy_unforced),
