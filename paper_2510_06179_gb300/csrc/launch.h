@@ -38,6 +38,11 @@ DMPC_DECLARE_TEAMS(rigid_body)
 DMPC_DECLARE_TEAMS(attitude)
 DMPC_DECLARE_TEAMS(mixed)
 
+// Raise a kernel's dynamic shared-memory limit to at least `smem` bytes on the current device.
+// The attribute is per device, so the largest size set so far is kept per (kernel, device);
+// a mutex makes concurrent callers (different host threads or devices) safe.
+cudaError_t raise_smem_limit(const void* kernel, size_t smem);
+
 // Fill `out` with every compiled kernel entry; returns the count (at most kMaxKernelEntries).
 constexpr int kMaxKernelEntries = 160;
 int collect_kernel_entries(KernelEntry* out);

@@ -8,12 +8,10 @@ namespace dmpc {
 
 template <int TEAM, class... Ms>
 cudaError_t launch_fused(const KParams& P, int grid, int threads, size_t smem, cudaStream_t s) {
-  static size_t configured = 0;  // largest dynamic smem size set so far for this kernel
   auto fn = fused_kernel<TEAM, Ms...>;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024) {
+    cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(fn), smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   fn<<<grid, threads, smem, s>>>(P);
   return cudaGetLastError();

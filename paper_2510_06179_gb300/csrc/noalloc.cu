@@ -100,7 +100,7 @@ extern "C" dmpc_err dmpc_solve_noalloc(const dmpc_ocp_desc* desc, int batch, con
   if (opt) o = *opt; else dmpc_default_options(&o);
   if (o.sqp_iters < 1 || o.sqp_iters > 1000 || o.n_alpha < 1 || o.n_alpha > 8 || !(o.pcg_tol > 0.f) ||
       !(o.pcg_tol < 1.f) || o.pcg_max_iters < 1 || !(o.ru_delta > 0.f && o.ru_delta < 1.f) ||
-      !(o.ls_eta > 0.f && o.ls_eta < 1.f) || (o.pcg_precision != 0 && o.pcg_precision != 1) ||
+      !(o.ls_eta > 0.f && o.ls_eta < 1.f) || !(o.feas_tol >= 0.f) || (o.pcg_precision != 0 && o.pcg_precision != 1) ||
       (o.exact_hessian != 0 && o.exact_hessian != 1))
     return DMPC_E_ARG;
   for (int i = 0; i < o.n_alpha; ++i)
@@ -136,13 +136,18 @@ extern "C" dmpc_err dmpc_solve_noalloc(const dmpc_ocp_desc* desc, int batch, con
   int tpb = o.teams_per_block > 0 ? o.teams_per_block : std::max(1, std::min(cap, batch / std::max(1, n_sm)));
   tpb = std::max(1, std::min(tpb, cap));
   int grid = (batch + tpb - 1) / tpb;
-  if (use_gws) grid = std::min(grid, 2 * n_sm);
 
-  // scratch budget: records + work list (+ per-team workspace in global memory)
+  // scratch budget: records + work list (+ per-team workspace in global memory).  Teams walk
+  // the work list (team g takes items g, g + G, ...), so any grid of at least one block
+  // covers the batch: with a global workspace the grid is capped by what fits in the array.
   const size_t rec_bytes = ((size_t)batch * sizeof(OcpRec) + 255) & ~(size_t)255;
   const size_t ord_bytes = ((size_t)batch * sizeof(int) + 255) & ~(size_t)255;
-  const size_t gws_bytes = use_gws ? (size_t)grid * tpb * ws_bytes : 0;
-  if (rec_bytes + ord_bytes + gws_bytes > kScratchBytes) return DMPC_E_BUDGET;
+  if (rec_bytes + ord_bytes > kScratchBytes) return DMPC_E_BUDGET;
+  if (use_gws) {
+    const size_t fit = (kScratchBytes - rec_bytes - ord_bytes) / ((size_t)tpb * ws_bytes);
+    if (fit < 1) return DMPC_E_BUDGET;
+    grid = (int)std::min<size_t>({(size_t)grid, (size_t)2 * n_sm, fit});
+  }
 
   LaunchFn fn = nullptr;
   {

@@ -1,7 +1,26 @@
-// Collects the kernel entries of every per-team kernel translation unit.
+// Collects the kernel entries of every per-team kernel translation unit, and keeps the
+// per-device dynamic shared-memory limits of the kernels.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "launch.h"
 
 namespace dmpc {
+cudaError_t raise_smem_limit(const void* kernel, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> configured;  // (kernel, device) -> bytes
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = configured[{kernel, dev}];
+  if (smem <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) cur = smem;
+  return e;
+}
+
 int collect_kernel_entries(KernelEntry* out) {
   int n = 0;
 #define DMPC_COLLECT(model)                          \
