@@ -225,6 +225,21 @@ dmpc_err dmpc_solve_noalloc(const dmpc_ocp_desc* desc, int batch, const dmpc_opt
                             const float* lam_init, float* z_out, float* lam_out, int* status_out,
                             int* pcg_iters_out, float* alpha_out);
 
+/* Measurement probes (the paper has no counterpart): the denominators the benchmark reports the
+ * fused kernel against.  Both run synchronously on the current device, allocate a few bytes of
+ * their own, time themselves with CUDA events (best of several repetitions) and are not meant
+ * for a solve loop.
+ *   dmpc_probe_fp32_peak: FP32 FMA throughput of the whole device in TFLOP/s (2 FLOP per FMA;
+ *     eight independent FMA chains per thread, two 1024-thread blocks per SM); *ms_out
+ *     (nullable) receives the timed launch's duration.
+ *   dmpc_probe_pcg_floor: microseconds per iteration of the fused kernel's single-warp PCG inner
+ *     loop (Algorithm 4 with nx = 4 and two knots per lane: two block-tridiagonal products, two
+ *     warp reductions, the scalar divisions and the vector updates), one warp alone on the GPU,
+ *     `iters` iterations (1 .. 2^24).  A PCG solve of k iterations takes at least k times it.
+ * Errors: DMPC_E_ARG (null output, iters out of range), DMPC_E_OOM, DMPC_E_CUDA. */
+dmpc_err dmpc_probe_fp32_peak(double* tflops_out, double* ms_out);
+dmpc_err dmpc_probe_pcg_floor(int iters, double* us_per_iter_out);
+
 /* Make (z, lam) with the inputs (x_s, theta, x_ref) the handle's resident solution, as if a
  * dmpc_solve had returned them: the next dmpc_vjp differentiates at that point (Algorithm 3
  * linearises at the given z, with lam as the multipliers).  Lets one handle serve several

@@ -47,6 +47,8 @@ SIGNATURES = {
     "dmpc_set_stream": (c_int, [P, P]),
     "dmpc_set_tiling": (c_int, [P, c_int, c_int]),
     "dmpc_get_tiling": (c_int, [P, P, P, P, P]),
+    "dmpc_probe_fp32_peak": (c_int, [P, P]),
+    "dmpc_probe_pcg_floor": (c_int, [c_int, P]),
     "dmpc_destroy": (None, [P]),
     "dmpc_last_error": (ctypes.c_char_p, [P]),
     "dmpc_version": (ctypes.c_char_p, []),
