@@ -16,7 +16,7 @@ Readings where the paper leaves a detail open:
 import numpy as np
 
 from .ocp import (linearise, solve_qp, split_z, join_z, cost_value, cost_gradient,
-                  constraint_residual)
+                  constraint_residual, kkt_residual)
 
 LS_ALPHAS = (1.0, 0.7, 0.3, 0.1, 0.01)
 LS_ETA = 0.4
@@ -61,17 +61,22 @@ def line_search(ocp, z, z_plus, alphas=LS_ALPHAS, eta=LS_ETA):
 
 
 def sqp(ocp, iters, line_search_on=True, alphas=LS_ALPHAS, eta=LS_ETA, z0=None, lam0=None,
-        dense=False):
+        dense=False, alpha_seq=None):
     """Algorithm 2 for a batch, a fixed number of iterations.
 
     Each iteration: linearise (Eq. 4), solve the QP exactly (Eq. 6), line search
-    (Algorithm 5) or a full step, then z <- z + alpha (z^+ - z), lambda likewise."""
+    (Algorithm 5) or a full step, then z <- z + alpha (z^+ - z), lambda likewise.
+
+    alpha_seq (B, iters), optional: take these step sizes instead of the line search's choice
+    (a replay of another run's path); the line search's test values are still evaluated at
+    every iterate and returned, with the oracle's own choice in "alpha_own"."""
     z, lam = cold_start(ocp)
     if z0 is not None:
         z = np.array(z0, dtype=np.float64)
     if lam0 is not None:
         lam = np.array(lam0, dtype=np.float64)
     hist_alpha = np.ones((ocp.B, iters))
+    hist_own = np.ones((ocp.B, iters))
     hist_delta = np.zeros((ocp.B, iters, len(alphas)))
     hist_phi0 = np.zeros((ocp.B, iters))
     for k in range(iters):
@@ -86,10 +91,13 @@ def sqp(ocp, iters, line_search_on=True, alphas=LS_ALPHAS, eta=LS_ETA, z0=None, 
             hist_phi0[:, k] = diag["phi0"]
         else:
             alpha = np.ones(ocp.B)
+        hist_own[:, k] = alpha
+        if alpha_seq is not None:
+            alpha = np.asarray(alpha_seq, dtype=np.float64)[:, k]
         z = z + alpha[:, None] * (zp - z)
         lam = lam + alpha[:, None] * (lp - lam)
         hist_alpha[:, k] = alpha
-    return dict(z=z, lam=lam, alpha=hist_alpha, delta=hist_delta, phi0=hist_phi0)
+    return dict(z=z, lam=lam, alpha=hist_alpha, alpha_own=hist_own, delta=hist_delta, phi0=hist_phi0)
 
 
 def solve_to_convergence(ocp, z0=None, lam0=None, tol=1e-13, max_iters=400, warm_iters=40):
@@ -111,3 +119,31 @@ def solve_to_convergence(ocp, z0=None, lam0=None, tol=1e-13, max_iters=400, warm
         if step <= tol:
             break
     return z, lam
+
+
+def newton_kkt(ocp, z0, lam0, tol=1e-13, max_iters=50):
+    """Newton's method on the KKT conditions F(z, lambda) = 0 of Eq. 1 (the textbook Newton-KKT
+    iteration, Nocedal and Wright Alg. 18.1): K [dz; dlambda] = -F with K the KKT matrix of the
+    EXACT Lagrangian Hessian (dynamics curvature included).  Converges quadratically from a point
+    near a strict local minimum, where full-step Gauss-Newton SQP need not converge at all (its
+    fixed-point map is not a contraction when the dynamics curvature weighted by the multipliers
+    is large against the cost Hessian).  Used to re-solve perturbed OCPs for finite differences;
+    not the paper's method.  Returns (z, lambda, final step, iterations)."""
+    from .backward import exact_hessian_blocks
+    z = np.array(z0, dtype=np.float64)
+    lam = np.array(lam0, dtype=np.float64)
+    step = np.inf
+    for it in range(1, max_iters + 1):
+        qp = linearise(ocp, z)
+        Fz, Fl = kkt_residual(ocp, z, lam)
+        dz = np.empty_like(z)
+        dl = np.empty_like(lam)
+        for b in range(ocp.B):
+            G = exact_hessian_blocks(ocp, z, lam, b)
+            dz[b], dl[b] = solve_qp(qp, b, rhs=-np.concatenate([Fz[b], Fl[b]]), G_blocks=G)
+        z = z + dz
+        lam = lam + dl
+        step = np.abs(dz).max()
+        if step <= tol:
+            break
+    return z, lam, step, it
