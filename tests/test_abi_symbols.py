@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "dmpc.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(dmpc_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(dmpc_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_the_boundary():
@@ -28,7 +28,7 @@ def test_library_loads_and_exports_every_declared_symbol():
     for name in _declared():
         assert hasattr(lib, name), name
     out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True, text=True).stdout
-    exported = set(re.findall(r"\b(dmpc_[a-z_]+)\b", out))
+    exported = set(re.findall(r"\b(dmpc_[a-z0-9_]+)\b", out))
     assert set(_declared()) <= exported
     assert set(_lib.SIGNATURES) == set(_declared())
 
