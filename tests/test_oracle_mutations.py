@@ -350,6 +350,17 @@ def _dF_dtheta_cost_rows_without_reference(mp):
     _patch_all(mp, BW, "dF_dtheta", mutant)
 
 
+def _dF_dtheta_fiala_columns_swapped(mp):
+    orig = BW.dF_dtheta
+
+    def mutant(ocp, z, lam, b, g=None, h=None):
+        M = orig(ocp, z, lam, b, g, h)
+        if ocp.model.name == "single_track":
+            M[:, [0, 1]] = M[:, [1, 0]]                                  # planted: mu <-> C_alpha
+        return M
+    _patch_all(mp, BW, "dF_dtheta", mutant)
+
+
 def _implicit_a_plus_transposed(mp):
     orig = O.linearise
 
@@ -418,6 +429,8 @@ CASES = {
                                                               SQP.test_line_search_closed_form_on_feasible_lq),
     "dF/dtheta cost-weight columns without the reference (Eq. 3)": (
         _dF_dtheta_cost_rows_without_reference, lambda: VJP.test_dF_dtheta_matches_differenced_residual("kin_bicycle")),
+    "dF/dtheta friction and cornering-stiffness columns swapped (vehicle, Eq. 3)": (
+        _dF_dtheta_fiala_columns_swapped, lambda: VJP.test_dF_dtheta_matches_differenced_residual("single_track")),
     "implicit integrator's A^+ transposed (Eq. 4)": (
         _implicit_a_plus_transposed,
         lambda: IMPL.test_implicit_linearisation_matches_differences(IMPL.workloads.cartpole_config)),
