@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=256, help="OCPs in the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement of the JSON line")
     ap.add_argument("--suite", default=None, help="also run the comparison suite and write it to this JSON file")
     ap.add_argument("--suite-only", action="store_true", help="run only the comparison suite")
     return ap.parse_args()
@@ -134,77 +135,75 @@ def _single_thread_env():
 
 def _oracle_chunk(args):
     os.environ.setdefault("OMP_NUM_THREADS", "1")
-    x_s, theta, x_ref, u_t, seed = args
+    x_s, theta, x_ref, u_t, alpha_seq = args
     from oracle.models import make_model
     from oracle.ocp import OCPBatch
     from oracle.sqp import sqp
     from oracle.backward import vjp
     ocp = OCPBatch(make_model("cartpole", dt=0.05), T, x_s.astype(np.float64), theta.astype(np.float64),
                    x_ref.astype(np.float64))
-    out = sqp(ocp, SQP_ITERS, line_search_on=True)
+    out = sqp(ocp, SQP_ITERS, line_search_on=True, alpha_seq=alpha_seq)
     z = out["z"]
     g = np.zeros_like(z)
     g[:, 4:5] = 2.0 * (z[:, 4:5] - u_t)
     res = vjp(ocp, z, out["lam"], g)
-    return z, res["dtheta"], out["alpha"], out["delta"], out["phi0"]
+    return z, res["dtheta"], out["alpha"], out["delta"], out["phi0"], out["alpha_own"]
 
 
 class OracleSample:
     """Result of a timed oracle run: rate (OCP/s), seconds, and per OCP the solution z, dl/dtheta,
-    the step sizes and, per SQP iteration, the line-search test values delta (one per candidate
-    step) and the merit phi0 at the iterate."""
+    the step sizes taken and, per SQP iteration, the line-search test values delta (one per
+    candidate step), the merit phi0 at the iterate and the oracle's own choice alpha_own (equal to
+    alpha unless a step-size path was replayed)."""
 
-    def __init__(self, rate, seconds, z, dtheta, alpha, delta, phi0):
+    def __init__(self, rate, seconds, z, dtheta, alpha, delta, phi0, alpha_own):
         self.rate, self.seconds = rate, seconds
         self.z, self.dtheta, self.alpha, self.delta, self.phi0 = z, dtheta, alpha, delta, phi0
+        self.alpha_own = alpha_own
 
 
-def run_oracle_sample(w, n, pool_size):
+def run_oracle_sample(w, n, pool_size, alpha_seq=None):
     """Time the FP64 oracle (solve + vjp) on the first n OCPs of the workload, parallel over
-    OCPs on pool_size processes (spawned, one thread each)."""
+    OCPs on pool_size processes (spawned, one thread each).  alpha_seq (n, SQP_ITERS): replay
+    these step sizes instead of the line search's choices (the parity protocol's replay)."""
     chunks = []
     per = max(1, math.ceil(n / pool_size))
     for s in range(0, n, per):
         e = min(n, s + per)
-        chunks.append((w.x_s[s:e], w.theta[s:e], w.x_ref[s:e], w.u_target[s:e], s))
+        a = None if alpha_seq is None else np.asarray(alpha_seq[s:e], np.float64)
+        chunks.append((w.x_s[s:e], w.theta[s:e], w.x_ref[s:e], w.u_target[s:e], a))
     ctx = mp.get_context("spawn")
     with ctx.Pool(len(chunks), initializer=_single_thread_env) as pool:
-        pool.map(_oracle_chunk, [(c[0][:1], c[1][:1], c[2][:1], c[3][:1], 0) for c in chunks])  # import warm-up
+        pool.map(_oracle_chunk, [(c[0][:1], c[1][:1], c[2][:1], c[3][:1], None) for c in chunks])  # import warm-up
         t0 = time.perf_counter()
         res = pool.map(_oracle_chunk, chunks)
         dt = time.perf_counter() - t0
     cat = lambda i: np.concatenate([r[i] for r in res])
-    return OracleSample(n / dt, dt, cat(0), cat(1), cat(2), cat(3), cat(4))
+    return OracleSample(n / dt, dt, cat(0), cat(1), cat(2), cat(3), cat(4), cat(5))
 
 
-def accuracy(z, dtheta, alpha, ref, tie=1e-5):
-    """Solution and gradient errors of the GPU results against the oracle, per the parity
-    protocol: OCPs whose step-size sequence equals the oracle's are gated (z <= 1e-4,
-    dl/dtheta <= 1e-3); the others are split into near-tie branches (at the first iteration
-    where the steps differ, some line-search test the two runs decided differently lies within
-    `tie` of zero relative to the merit) and other branches."""
-    n = ref.z.shape[0]
+def accuracy(z, dtheta, alpha, own, rep, tie=1e-5):
+    """Solution and gradient errors of the GPU results against the FP64 oracle under the replay
+    protocol (oracle/protocol.py).  own: the oracle run along its own line-search path (the timed
+    CPU baseline); rep: the oracle replaying the GPU's step sizes, logging its tests at every
+    iterate.  Every OCP is gated: its path must be consistent with the oracle's tests up to
+    tie |phi| (a choice the line search allows within rounding), its solution within 1e-4 of the
+    replay and its dl/dtheta within 1e-3 of the oracle's gradient at the replay's solution."""
+    from oracle.protocol import path_consistency
+    n = rep.z.shape[0]
     z, dtheta, alpha = z[:n], dtheta[:n], alpha[:n]
-    ez = np.linalg.norm(z - ref.z, axis=1) / np.linalg.norm(ref.z, axis=1)
-    eg = np.linalg.norm(dtheta - ref.dtheta, axis=1) / np.maximum(np.linalg.norm(ref.dtheta, axis=1), 1e-30)
-    a32, r32 = alpha.astype(np.float32), ref.alpha.astype(np.float32)
-    agree = np.all(a32 == r32, axis=1)
-    alphas = np.array([1.0, 0.7, 0.3, 0.1, 0.01], np.float32)
-    near_tie = np.zeros(n, bool)
-    for b in np.where(~agree)[0]:
-        i = int(np.argmax(a32[b] != r32[b]))
-        jg = int(np.argmin(np.abs(alphas - a32[b, i])))
-        jo = int(np.argmin(np.abs(alphas - r32[b, i])))
-        marg = np.abs(ref.delta[b, i, :max(jg, jo) + 1]).min() / max(abs(ref.phi0[b, i]), 1e-30)
-        near_tie[b] = marg < tie
-    f = lambda v: float(v.max()) if v.size else None
-    return {"checked": int(n), "alpha_path_agree": int(agree.sum()),
-            "z_rel_err_max_agree": f(ez[agree]), "dtheta_rel_err_max_agree": f(eg[agree]),
-            "agree_within_gates": int(((ez <= 1e-4) & (eg <= 1e-3) & agree).sum()),
-            "branched_near_tie": int(near_tie.sum()), "branched_other": int((~agree & ~near_tie).sum()),
-            "branched_z_within_1e-4": int(((ez <= 1e-4) & ~agree).sum()),
-            "z_within_1e-4_all": int((ez <= 1e-4).sum()), "dtheta_within_1e-3_all": int((eg <= 1e-3).sum()),
-            "z_rel_err_median": float(np.median(ez))}
+    rel = lambda a, b: np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-30)
+    ez, eg = rel(z, rep.z), rel(dtheta, rep.dtheta)
+    consistent, _ = path_consistency(alpha, {"delta": rep.delta, "phi0": rep.phi0}, tie=tie)
+    own_path = np.all(alpha.astype(np.float32) == own.alpha[:n].astype(np.float32), axis=1)
+    gated = consistent & (ez <= 1e-4) & (eg <= 1e-3)
+    return {"checked": int(n), "protocol": "FP64 oracle replaying the GPU's step sizes; every step a choice "
+                                           f"the oracle's line-search tests allow within {tie:g} |phi|",
+            "path_consistent": int(consistent.sum()), "own_path": int(own_path.sum()),
+            "z_rel_err_max": float(ez.max()), "z_rel_err_median": float(np.median(ez)),
+            "dtheta_rel_err_max": float(eg.max()), "within_both_gates": int(gated.sum()),
+            "fraction_within_both_gates": round(float(gated.mean()), 4),
+            "z_rel_err_max_own_path": float(ez[own_path].max()) if own_path.any() else None}
 
 
 # ---------------------------------------------------------------------- clocks
@@ -272,6 +271,52 @@ def algorithmic_flops(pcg_iters_fwd, pcg_iters_bwd, nx=4, nu=1):
     fwd = B * SQP_ITERS * (lin + schur + prec + rec + ls) + per_iter * float(pcg_iters_fwd)
     bwd = B * (lin + schur + prec + rec + T * F_HD) + per_iter * float(pcg_iters_bwd)
     return fwd, bwd
+
+
+def measured_probes():
+    """(FP32 FMA peak in TFLOP/s, microseconds per FP32 PCG iteration of one warp alone) from the
+    library's probes, or (None, None) if a probe fails."""
+    import ctypes
+    from paper_2510_06179_gb300 import _lib
+    lib = _lib.load()
+    tf, ms, us = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    peak = tf.value if lib.dmpc_probe_fp32_peak(ctypes.byref(tf), ctypes.byref(ms)) == 0 else None
+    floor = us.value if lib.dmpc_probe_pcg_floor(20000, ctypes.byref(us)) == 0 else None
+    return peak, floor
+
+
+SERVING_RATE = 5000
+SERVING_REQUESTS = 1500
+
+
+def serving_bench(dev, rate=SERVING_RATE, n_requests=SERVING_REQUESTS):
+    """Continuous-batching serving at one Poisson arrival rate over a fixed number of requests,
+    fused and plain forms on the same trace: p50 / p99 latency (host arrival to device completion)
+    and completed requests per second.  Each form first serves a warm-up trace (not reported)."""
+    from paper_2510_06179_gb300 import workloads
+    from paper_2510_06179_gb300.serving import ServingEngine, Request, latency_stats
+    res = {"rate_per_s": rate, "requests": n_requests, "sqp_iters_per_request": 5, "pcg_tol": PCG_TOL,
+           "mix": "nx in {2, 4, 6, 12} uniform (pendulum, cart-pole, single-track, rigid body), "
+                  "T log-uniform in [16, 256], Poisson arrivals",
+           "latency": "host arrival to device completion of the request's last SQP iteration"}
+    for plain in (False, True):
+        eng = ServingEngine(workloads.SERVING_SHAPES, budget_bytes=64 << 30, sqp_iters=5, slots_per_class=256,
+                            plain=plain, pcg_tol=PCG_TOL)
+        warm = [Request(rid=i, **d) for i, d in enumerate(workloads.serving_trace(1000, 0.2, seed=1))]
+        eng.run(warm, max_seconds=60.0)
+        trace = workloads.serving_trace(rate, n_requests / rate, seed=rate)
+        reqs = [Request(rid=i, **d) for i, d in enumerate(trace)]
+        t0 = time.perf_counter()
+        eng.run(reqs, max_seconds=120.0)
+        wall = time.perf_counter() - t0
+        st = latency_stats(reqs)
+        res["requests"] = len(reqs)
+        res["plain" if plain else "fused"] = {
+            "p50_ms": round(st["p50_ms"], 3) if st["p50_ms"] is not None else None,
+            "p99_ms": round(st["p99_ms"], 3) if st["p99_ms"] is not None else None,
+            "completed": st["completed"], "completed_per_s": round(st["completed"] / wall, 1)}
+        eng.close()
+    return res
 
 
 def alu_peak_tflops(sm_mhz):
@@ -405,17 +450,34 @@ def main():
     f_fwd, f_bwd = algorithmic_flops(pcg_f, pcg_b)
     fwd_avg = float(np.mean(fwd_ms)) / 1e3
     achieved = f_fwd / fwd_avg / 1e12
-    peak = alu_peak_tflops(sm_mhz)
+    peak_meas, floor_us = measured_probes()
+    peak = peak_meas or alu_peak_tflops(sm_mhz)
     roof = {"bound": "alu", "kernel": "fused_kernel<32,CartPole> (forward, 10 SQP iterations)",
             "achieved": round(achieved, 4), "peak": round(peak, 2), "unit": "TFLOP/s",
             "frac": round(achieved / peak, 5), "traffic": captured_traffic(),
-            "peak_basis": f"152 SM x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock under load)",
+            "peak_basis": ("measured: dmpc_probe_fp32_peak (eight FMA chains per thread on every SM)" if peak_meas
+                           else f"derived: 152 SM x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"),
             "flops_per_launch": f_fwd, "avg_launch_ms": round(fwd_avg * 1e3, 4)}
+    iters_ocp = out["pcg_iters"].view(B, SQP_ITERS).sum(1).cpu().numpy()
+    latency = None
+    if floor_us:
+        worst = int(iters_ocp.max())
+        bound_ms = worst * floor_us / 1e3
+        latency = {"bound": "latency", "floor_us_per_pcg_iter": round(floor_us, 4),
+                   "floor_basis": "dmpc_probe_pcg_floor: one warp alone running the kernel's FP32 PCG iteration "
+                                  "(nx 4, two knots per lane)",
+                   "worst_ocp_pcg_iters": worst, "mean_ocp_pcg_iters": round(float(iters_ocp.mean()), 1),
+                   "bound_ms": round(bound_ms, 4), "avg_launch_ms": round(fwd_avg * 1e3, 4),
+                   "frac": round(bound_ms / (fwd_avg * 1e3), 4),
+                   "note": "the launch lasts as long as its slowest OCP's serial PCG chain; double-float rescue "
+                           "iterations are counted at the FP32 floor, so the bound is a lower bound"}
     acc = None
     if cpu is not None:
+        alpha_g = out["alpha"].view(B, SQP_ITERS).cpu().numpy()
+        rep = run_oracle_sample(w, n_cpu, os.cpu_count() or 1, alpha_seq=alpha_g[:n_cpu])
         acc = accuracy(out["z"].view(B, nz).cpu().numpy().astype(np.float64),
-                       gout["dtheta"].view(B, -1).cpu().numpy().astype(np.float64),
-                       out["alpha"].view(B, SQP_ITERS).cpu().numpy(), ref)
+                       gout["dtheta"].view(B, -1).cpu().numpy().astype(np.float64), alpha_g, ref, rep)
+    serving = None if args.no_serving else serving_bench(dev)
     tiling = batch.get_tiling()
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -429,12 +491,14 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": 2 * args.steps,
         "roofline": roof,
+        "latency_roofline": latency,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "accuracy": acc,
         "pcg_iters_per_qp": round(pcg_f / (B * SQP_ITERS), 2),
         "pcg_iters_per_s": round(pcg_f / fwd_avg, 1),   # forward-pass PCG iterations, all OCPs
         "status_nonzero": int((status & ~4).astype(bool).sum()),
+        "serving": serving,
     }
     print(json.dumps(line))
     if world > 1:
@@ -621,7 +685,7 @@ def suite(path):
     # one-iteration MPC solves on one handle, reward gradient through every solve
     from paper_2510_06179_gb300 import rollout
     rl = {}
-    for pid in (1, 2, 3, 4):
+    for pid in (1, 2, 3, 4, 5, 6):
         prob = workloads.rl_lq_problem(pid, seed=0)
         batch = rollout.make_batch(prob, dev, pcg_tol=1e-9)
         env = rollout.env_tensors(prob, dev)

@@ -48,6 +48,8 @@ class Request:
     done: float = None          # completion time (s)
     z: np.ndarray = None        # solution (n,) float32
     status: int = None
+    alpha: np.ndarray = None    # step size of each SQP iteration (kept with the solution)
+    alpha_refs: list = field(default_factory=list, repr=False)   # (tick buffer, slot) per iteration
 
 
 class SlotClass:
@@ -68,6 +70,7 @@ class SlotClass:
         # busy-slot list of the tick: pinned staging and device copy, reused (one tick in flight)
         self.idx_h = torch.zeros(slots, dtype=torch.int32).pin_memory()
         self.idx_d = torch.zeros(slots, dtype=torch.int32, device=device)
+        self.slots = slots
         self.free = deque(range(slots))
         self.busy = {}              # slot -> [request, ticks launched]
         self.queue = deque()
@@ -107,8 +110,10 @@ class SlotClass:
                                               descs, reset.ctypes.data_as(ctypes.c_void_p)), b.h)
         return len(new)
 
-    def advance(self, plain):
-        """One SQP iteration on every busy slot (one launch); records the tick in flight."""
+    def advance(self, plain, record_alpha=False):
+        """One SQP iteration on every busy slot (one launch); records the tick in flight.  With
+        record_alpha each tick writes its step sizes to a buffer of its own, so every request
+        can later read the step size of each of its iterations."""
         if not self.busy:
             return False
         b = self.batch
@@ -119,13 +124,16 @@ class SlotClass:
             self.idx_d[:n].copy_(self.idx_h[:n], non_blocking=True)
             fn = self.lib.dmpc_solve_subset_plain if plain else self.lib.dmpc_solve_subset
             ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+            alpha = torch.zeros(self.slots, device=self.device) if record_alpha else None
             _lib.check(fn(b.h, ptr(self.idx_d), n, ptr(self.x_s), ptr(self.theta), ptr(self.x_ref), ptr(self.z),
-                          ptr(self.lam), ptr(self.status), None, None), b.h)
+                          ptr(self.lam), ptr(self.status), None, ptr(alpha) if record_alpha else None), b.h)
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(self.stream)
         done = []
         for s in slots.tolist():
             st = self.busy[s]
+            if record_alpha:
+                st[0].alpha_refs.append((alpha, s))
             st[1] += 1
             if st[1] >= b.sqp_iters_total:
                 done.append((s, self.busy.pop(s)[0]))   # not advanced again; freed when retired
@@ -146,6 +154,9 @@ class SlotClass:
                 n = r.nx * (r.T + 1) + r.nu * r.T
                 r.z = self.z[b.z_off[s]:b.z_off[s] + n].detach().cpu().numpy().copy()
                 r.status = int(self.status[s].item())
+                if r.alpha_refs:
+                    r.alpha = np.array([float(a[i].item()) for a, i in r.alpha_refs], dtype=np.float32)
+                    r.alpha_refs = []
             self.free.append(s)
         return len(done)
 
@@ -218,7 +229,7 @@ class ServingEngine:
                     continue
                 n_done += c.retire(start_ev, keep_solutions)
                 c.admit()
-                active = c.advance(self.plain) or active
+                active = c.advance(self.plain, record_alpha=keep_solutions) or active
             if not active and pending:
                 time.sleep(max(0.0, min(1e-4, pending[0].arrival - (time.perf_counter() - t0))))
         for c in classes:

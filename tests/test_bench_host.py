@@ -1,5 +1,6 @@
-"""Host logic of the benchmark (no GPU): gating of agreeing step-size paths and the near-tie
-classification of branched ones in the accuracy report, and the reference arm's output line."""
+"""Host logic of the benchmark (no GPU): the accuracy report's replay protocol (path consistency
+with the oracle's line-search tests, gates against the replay), and the reference arm's output
+line."""
 import numpy as np
 
 import bench
@@ -12,34 +13,37 @@ def _ref(n=4, iters=3):
     alpha = np.ones((n, iters))
     delta = -np.ones((n, iters, 5))          # every candidate passes clearly
     phi0 = np.full((n, iters), 10.0)
-    return bench.OracleSample(100.0, 1.0, z, dth, alpha, delta, phi0)
+    return bench.OracleSample(100.0, 1.0, z, dth, alpha, delta, phi0, alpha.copy())
 
 
-def test_identical_results_all_agree():
-    ref = _ref()
-    acc = bench.accuracy(ref.z.copy(), ref.dtheta.copy(), ref.alpha.copy(), ref)
-    assert acc["alpha_path_agree"] == 4 and acc["agree_within_gates"] == 4
-    assert acc["branched_near_tie"] == 0 and acc["branched_other"] == 0
-    assert acc["z_rel_err_max_agree"] == 0.0
+def test_identical_results_all_within_gates():
+    own = _ref()
+    rep = _ref()
+    acc = bench.accuracy(own.z.copy(), own.dtheta.copy(), own.alpha.copy(), own, rep)
+    assert acc["own_path"] == 4 and acc["path_consistent"] == 4 and acc["within_both_gates"] == 4
+    assert acc["z_rel_err_max"] == 0.0 and acc["fraction_within_both_gates"] == 1.0
 
 
-def test_branch_classification_and_gates():
-    ref = _ref()
-    z, dth, al = ref.z.copy(), ref.dtheta.copy(), ref.alpha.copy()
-    # OCP 1 branches at iteration 1 where the alpha = 1 test was a near tie
+def test_replay_protocol_gates_every_ocp():
+    own = _ref()
+    rep = _ref()
+    z, dth, al = own.z.copy(), own.dtheta.copy(), own.alpha.copy()
+    # OCP 1 took 0.7 at iteration 1 where the alpha = 1 test was a near tie (fails by 1e-7 |phi|):
+    # consistent; its solution is gated against the replay (identical here)
     al[1, 1] = 0.7
-    ref.delta[1, 1, 0] = 1e-7
-    # OCP 2 branches at iteration 2 with clear margins
+    rep.alpha[1, 1] = 0.7
+    rep.delta[1, 1, 0] = 1e-6
+    # OCP 2 took 0.3 at iteration 2 although alpha = 1 passed clearly: inconsistent
     al[2, 2] = 0.3
-    # OCP 3 agrees but its solution is off by 1e-3
+    rep.alpha[2, 2] = 0.3
+    # OCP 3 follows the oracle's path but its solution is off by 1e-3
     z[3] *= 1.001
-    acc = bench.accuracy(z, dth, al, ref)
-    assert acc["alpha_path_agree"] == 2
-    assert acc["branched_near_tie"] == 1 and acc["branched_other"] == 1
-    assert acc["agree_within_gates"] == 1
-    assert abs(acc["z_rel_err_max_agree"] - 1e-3) < 1e-9
-    assert acc["z_within_1e-4_all"] == 3
-    assert acc["branched_z_within_1e-4"] == 2     # OCPs 1 and 2 branched but kept their solutions
+    acc = bench.accuracy(z, dth, al, own, rep)
+    assert acc["own_path"] == 2
+    assert acc["path_consistent"] == 3
+    assert acc["within_both_gates"] == 2           # OCP 2 (path) and OCP 3 (solution) fail
+    assert abs(acc["z_rel_err_max"] - 1e-3) < 1e-9
+    assert acc["fraction_within_both_gates"] == 0.5
 
 
 def test_serving_class_priorities_order_by_cost():

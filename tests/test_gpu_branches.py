@@ -17,17 +17,24 @@ from tests.oracle_helpers import to_ocp, rel_err
 
 pytestmark = pytest.mark.gpu
 
-B, T, SEED = 64, 50, 1000
+CASES = {
+    "cartpole": lambda: workloads.cartpole_config(B=64, T=50, seed=1000, sqp_iters=10),
+    "pendulum": lambda: workloads.pendulum_config(B=64, T=40, seed=7, sqp_iters=10),
+    "kin_bicycle": lambda: workloads.bicycle_config(B=64, T=40, seed=7, sqp_iters=10),
+    "attitude": lambda: workloads.attitude_config(B=64, seed=7, sqp_iters=10),
+}
 
 
-def test_branched_ocps_end_at_kkt_points():
-    w = workloads.cartpole_config(B=B, T=T, seed=SEED, sqp_iters=10)
+@pytest.mark.parametrize("name", list(CASES))
+def test_branched_ocps_end_at_kkt_points(name):
+    w = CASES[name]()
+    B = w.B
     b10, g10 = gpu_solve(w, pcg_tol=5e-8, warm_start=0)
     b10.close()
     ocp_all = to_ocp(w)
-    ref10 = oracle_sqp(ocp_all, 10, line_search_on=True)
+    ref10 = oracle_sqp(ocp_all, w.sqp_iters, line_search_on=True)
     br = np.where(~alpha_paths_agree(g10["alpha"], ref10["alpha"]))[0]
-    print(f"cart-pole {B}: {len(br)} OCPs branched after 10 SQP iterations")
+    print(f"{name} {B}: {len(br)} OCPs branched after {w.sqp_iters} SQP iterations")
     if len(br) == 0:
         return
     # the GPU on from its own iterate: 100 full SQP steps (Gauss-Newton converges linearly)
