@@ -23,7 +23,7 @@
  *    Costs: c_t^x(x) = 1/2 (x - x_ref,t)^T diag(Q) (x - x_ref,t)  (diag(Q_T) at t = T),
  *           c_t^u(u) = 1/2 u^T diag(R) u.
  *  - Models (f_t = x_{t+1} - Phi_t(x_t, u_t), Phi one RK4 / Euler step, or affine):
- *      LQ           any nx, nu in {(2,1),(3,2),(4,1),(8,4)}; p_s = 0; per knot
+ *      LQ           nx, nu in {(2,1),(3,2),(4,1),(8,4),(16,8)} ((16,8): 32-thread teams); p_s = 0; per knot
  *                   p_k = nx*nx + nx*nu + nx: Abar_t (row-major), Bbar_t, c_t
  *      PENDULUM     nx 2, nu 1, params (m, L)                 RK4
  *      CARTPOLE     nx 4, nu 1, params (m_pole, L), m_cart 1  RK4
@@ -31,6 +31,11 @@
  *      SINGLE_TRACK nx 6, nu 2, params (mu, C_alpha)          RK4 (Fiala tyres)
  *      RIGID_BODY12 nx 12, nu 4, params (m, Jx, Jy, Jz)       RK4
  *      ATTITUDE     nx 3, nu 3, params (J1, J2, J3)           forward Euler
+ *      SINGLE_TRACK_RATE  nx 8, nu 2, params (mu, C_alpha): the vehicle with control-rate
+ *                   augmentation (App. B.3): state (x, delta, F_x), input their rates;
+ *                   x_{t+1} = Phi_t(x_t, (delta_t, F_x,t)) by RK4, (delta, F_x)_{t+1} =
+ *                   (delta, F_x)_t + dt u_t, so diag R weighs the control rates; not mixed
+ *                   with other models in one batch
  *  - Calls are asynchronous on the handle's CUDA stream and return a dmpc_err for argument
  *    and launch errors.  Numerical outcomes are per OCP in status_out (bit flags below); a
  *    failed OCP never aborts the batch and the device never traps.
@@ -76,7 +81,8 @@ typedef enum {
   DMPC_MODEL_KIN_BICYCLE = 3,
   DMPC_MODEL_SINGLE_TRACK = 4,
   DMPC_MODEL_RIGID_BODY12 = 5,
-  DMPC_MODEL_ATTITUDE = 6
+  DMPC_MODEL_ATTITUDE = 6,
+  DMPC_MODEL_SINGLE_TRACK_RATE = 7  /* SINGLE_TRACK with control-rate augmentation (App. B.3) */
 } dmpc_model;
 
 /* Integrator of a continuous model (dmpc_ocp_desc.integrator). */
@@ -120,6 +126,10 @@ typedef struct {
                           dynamics curvature weighted by the forward multipliers, Sec. 3.4), so the
                           gradient is exact for nonlinear dynamics; 0: Gauss-Newton (the paper's
                           default); enlarges the workspace by (nx+nu)^2 doubles per knot; default 0 */
+  int pcg_variant;     /* 0: Algorithm 4 as printed (two dependent reductions per iteration); 1: the same
+                          iteration reorganised after Chronopoulos and Gear (one fused reduction of r^T u
+                          and (S u)^T u per iteration, S p by recurrence; equal in exact arithmetic);
+                          single-warp teams (nx <= 4, K <= 64), the others behave as 0; default 0 */
 } dmpc_options;
 
 /* Fill *opt with the defaults above. */
@@ -160,10 +170,12 @@ dmpc_err dmpc_vjp(dmpc_handle* h, const float* dl_dz, float* dl_dtheta, float* d
 /* The plain one-launch-per-step form of the same method, for comparison: identical arguments,
  * results and resident state as dmpc_solve / dmpc_vjp (they may be mixed on one handle), but
  * every step (linearise, Schur blocks, preconditioner, each PCG operation of Algorithm 4,
- * recovery, line search) is a separate kernel launch over the batch, the per-OCP workspace
- * (the S and Phi^-1 blocks included) lives in HBM, and the host polls PCG convergence every
- * 8 iterations (a device-to-host copy and a stream synchronisation).  Blocking: returns after
- * the last poll; the final launches are asynchronous.  Stored-Schur mode is not used. */
+ * recovery, line search) is a separate kernel launch over the batch and the per-OCP workspace
+ * (the S and Phi^-1 blocks included) lives in HBM.  The launches of one call form a CUDA graph
+ * (captured on the handle's first plain call, and again after a tiling change) in which each PCG
+ * solve is a conditional WHILE node: it repeats eight PCG iterations until no OCP is still
+ * iterating, decided on the device, with no host synchronisation.  Asynchronous on the handle's
+ * stream.  Stored-Schur mode is not used. */
 dmpc_err dmpc_solve_plain(dmpc_handle* h, const float* x_s, const float* theta, const float* x_ref,
                           const float* z_init, const float* lam_init, float* z_out, float* lam_out,
                           int* status_out, int* pcg_iters_out, float* alpha_out);

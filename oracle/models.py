@@ -254,8 +254,36 @@ class Attitude(Model):
         return [(c1 + u[0]) / j1, (c2 + u[1]) / j2, (c3 + u[2]) / j3]
 
 
+class ControlRate(Model):
+    """Control-rate augmentation of a base model (App. B.3: the vehicle's cost on control rates
+    is implemented by augmenting the state with the input, x <- (x, u), and taking the rate of the
+    input as the new input, u <- u_dot).  State (x, u) of size nx_b + nu_b, input v (nu_b):
+      x_{t+1} = Phi_t(x_t, u_t)   (the base model's step, with the input held in the state),
+      u_{t+1} = u_t + dt v_t,
+    so v_t = (u_{t+1} - u_t) / dt, and the input cost 1/2 v^T diag(R) v penalises the rate while
+    diag(Q) over (x, u) weighs the state and the input itself.  Same parameters as the base."""
+    integrator = "rate"
+
+    def __init__(self, base):
+        super().__init__(base.dt)
+        self.base = base
+        self.name = base.name + "_rate"
+        self.nx = base.nx + base.nu
+        self.nu = base.nu
+        self.p_shared = base.p_shared
+        self.p_knot = base.p_knot
+
+    def step(self, x, u, ths, thk):
+        nb = self.base.nx
+        xb, ub = list(x[:nb]), list(x[nb:])
+        return list(self.base.step(xb, ub, ths, thk)) + [ub[i] + self.dt * u[i] for i in range(self.nu)]
+
+
 def make_model(name, nx=None, nu=None, dt=0.05, integrator=None):
-    """integrator: None (the model's own) or "trapezoid" (implicit trapezoidal rule)."""
+    """integrator: None (the model's own) or "trapezoid" (implicit trapezoidal rule).  A name
+    ending in "_rate" is the control-rate augmentation of the named model."""
+    if name.endswith("_rate"):
+        return ControlRate(make_model(name[:-len("_rate")], dt=dt, integrator=integrator))
     if name == "lq":
         return LQ(nx, nu)
     table = {"pendulum": Pendulum, "cartpole": CartPole, "kin_bicycle": KinematicBicycle,

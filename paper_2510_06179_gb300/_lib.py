@@ -23,7 +23,7 @@ class dmpc_options(ctypes.Structure):
                 ("ls_eta", c_float), ("feas_tol", c_float), ("pcg_tol", c_float), ("pcg_max_iters", c_int),
                 ("ru_delta", c_float), ("warm_start", c_int), ("store_schur", c_int),
                 ("team_threads", c_int), ("teams_per_block", c_int), ("pcg_precision", c_int),
-                ("exact_hessian", c_int)]
+                ("exact_hessian", c_int), ("pcg_variant", c_int)]
 
 
 SIGNATURES = {

@@ -19,17 +19,13 @@
 using namespace dmpc;
 
 namespace dmpc {
-__global__ void plain_count_active(const PlainState* st, const int* order, int n, int* out) {
-  __shared__ int part[256];
-  int acc = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += st[order ? order[i] : i].active;
-  part[threadIdx.x] = acc;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = part[0];
+__global__ void plain_pcg_continue(const PlainState* st, const KParams* P, cudaGraphConditionalHandle cond) {
+  const int n = P->n_work;
+  const int* order = P->order;
+  int any = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) any |= st[order ? order[i] : i].active;
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);
 }
 }  // namespace dmpc
 
@@ -42,7 +38,8 @@ struct ModelInfo {
 bool model_info(int model, int nx, int nu, ModelInfo* mi) {
   switch (model) {
     case DMPC_MODEL_LQ:
-      if (!((nx == 2 && nu == 1) || (nx == 3 && nu == 2) || (nx == 4 && nu == 1) || (nx == 8 && nu == 4)))
+      if (!((nx == 2 && nu == 1) || (nx == 3 && nu == 2) || (nx == 4 && nu == 1) || (nx == 8 && nu == 4) ||
+            (nx == 16 && nu == 8)))
         return false;
       *mi = {nx, nu, 0, I_AFFINE};
       return true;
@@ -52,6 +49,7 @@ bool model_info(int model, int nx, int nu, ModelInfo* mi) {
     case DMPC_MODEL_SINGLE_TRACK: *mi = {6, 2, 2, I_RK4}; break;
     case DMPC_MODEL_RIGID_BODY12: *mi = {12, 4, 4, I_RK4}; break;
     case DMPC_MODEL_ATTITUDE: *mi = {3, 3, 3, I_EULER}; break;
+    case DMPC_MODEL_SINGLE_TRACK_RATE: *mi = {8, 2, 2, I_RATE}; break;
     default: return false;
   }
   return mi->nx == nx && mi->nu == nu;
@@ -134,8 +132,11 @@ struct dmpc_handle {
   size_t bytes = 0;
   float* plain_ws = nullptr;
   PlainState* plain_st = nullptr;
-  int* plain_dcount = nullptr;
-  int* plain_hcount = nullptr;
+  KParams* plain_params = nullptr;     // device copy of the plain form's launch parameters
+  cudaStream_t plain_cap[2] = {nullptr, nullptr};  // capture streams (main sequence, PCG bodies)
+  cudaGraphExec_t plain_graph[2] = {nullptr, nullptr};  // instantiated forward / backward graphs
+  PlainFn plain_graph_fn[2] = {nullptr, nullptr};       // kernel set each graph was captured with
+  int plain_graph_team[2] = {0, 0};
   int plain_ws_floats = 0;
   std::string err;
 };
@@ -168,6 +169,7 @@ extern "C" void dmpc_default_options(dmpc_options* o) {
   o->teams_per_block = 0;
   o->pcg_precision = 0;
   o->exact_hessian = 0;
+  o->pcg_variant = 0;
 }
 
 static Options to_kernel_options(const dmpc_options& o) {
@@ -184,6 +186,7 @@ static Options to_kernel_options(const dmpc_options& o) {
   k.ru_delta = o.ru_delta;
   k.pcg_precision = o.pcg_precision;
   k.exact_hessian = o.exact_hessian;
+  k.pcg_variant = o.pcg_variant;
   return k;
 }
 
@@ -203,6 +206,7 @@ static dmpc_err validate_options(dmpc_handle* h, const dmpc_options& o) {
   if (o.teams_per_block < 0) return fail(h, DMPC_E_ARG, "teams_per_block must be >= 0");
   if (o.pcg_precision != 0 && o.pcg_precision != 1) return fail(h, DMPC_E_ARG, "pcg_precision must be 0 or 1");
   if (o.exact_hessian != 0 && o.exact_hessian != 1) return fail(h, DMPC_E_ARG, "exact_hessian must be 0 or 1");
+  if (o.pcg_variant != 0 && o.pcg_variant != 1) return fail(h, DMPC_E_ARG, "pcg_variant must be 0 or 1");
   return DMPC_OK;
 }
 
@@ -212,6 +216,7 @@ static dmpc_err configure_tiling(dmpc_handle* h, int team, int tpb) {
   for (auto& d : h->descs) maxK = std::max(maxK, d.T + 1);
   int maxnx = 0;
   for (auto& d : h->descs) maxnx = std::max(maxnx, d.nx);
+  const bool team_is_default = team == 0;
   if (team == 0) {
     // one knot per lane (register-resident PCG) when it fits, else a few knots per lane:
     // nx <= 4: one warp with one or two knots per lane up to K = 64; nx <= 6: one knot per lane
@@ -220,6 +225,16 @@ static dmpc_err configure_tiling(dmpc_handle* h, int team, int tpb) {
       team = maxK <= 64 ? (maxnx <= 4 ? 32 : 64) : (maxK <= 128 ? 128 : 256);
     else
       team = maxK <= 32 ? 32 : (maxK <= 64 ? 64 : (maxK <= 320 ? 128 : 256));
+  }
+  if (h->uniform && team_is_default) {
+    // a shape compiled for fewer team sizes (LQ with nx = 16: 32 threads) takes the one it has
+    bool have = false;
+    for (auto& e : registry()) have |= e.team == team && e.model == h->model0 && e.nx == h->nx0 && e.nu == h->nu0;
+    for (int alt : {32, 64, 128, 256}) {
+      if (have) break;
+      for (auto& e : registry())
+        if (e.team == alt && e.model == h->model0 && e.nx == h->nx0 && e.nu == h->nu0) { team = alt; have = true; break; }
+    }
   }
   int ws = 0;
   for (auto& d : h->descs) ws = std::max(ws, make_layout(d.nx, d.nu, d.T + 1, team, h->opt.exact_hessian, is_implicit_desc(d)).total_floats);
@@ -241,9 +256,15 @@ static dmpc_err configure_tiling(dmpc_handle* h, int team, int tpb) {
     if (h->uniform && e.model == h->model0 && e.nx == h->nx0 && e.nu == h->nu0) { fn = e.fn; pfn = e.plain; break; }
   }
   if (!fn) {
-    bool has_lq = false, has_implicit = false;
-    for (auto& d : h->descs) { has_lq |= d.model == DMPC_MODEL_LQ; has_implicit |= is_implicit_desc(d) != 0; }
+    bool has_lq = false, has_implicit = false, has_rate = false;
+    for (auto& d : h->descs) {
+      has_lq |= d.model == DMPC_MODEL_LQ;
+      has_implicit |= is_implicit_desc(d) != 0;
+      has_rate |= d.model == DMPC_MODEL_SINGLE_TRACK_RATE;
+    }
     if (has_lq) return fail(h, DMPC_E_UNSUPPORTED, "LQ OCPs cannot be mixed with other models in one batch");
+    if (has_rate)
+      return fail(h, DMPC_E_UNSUPPORTED, "control-rate OCPs cannot be mixed with other models in one batch");
     if (has_implicit)
       return fail(h, DMPC_E_UNSUPPORTED, "implicit-integrator OCPs cannot be mixed with other models in one batch");
     for (auto& e : registry())
@@ -526,9 +547,12 @@ extern "C" dmpc_err dmpc_qp_inspect(dmpc_handle* h, const float* x_s, const floa
 
 // ---------------------------------------------------------------------------------------
 // Plain one-launch-per-step form (the comparator of the fused kernel): the same stages, one
-// launch per step over the batch, per-OCP workspace in HBM, convergence polled by the host
-// every kPlainPoll PCG iterations.
-static const int kPlainPoll = 8;
+// launch per step over the batch, per-OCP workspace in HBM.  All launches of a solve (or a vjp)
+// form one CUDA graph, captured once per handle: each PCG solve is a conditional WHILE node
+// whose body runs kPlainUnroll PCG iterations (four launches each) and plain_pcg_continue, which
+// ends the loop on the device once no OCP is still iterating.  The launch parameters live in
+// device memory (plain_params), written with one copy before each graph launch.
+static const int kPlainUnroll = 8;
 
 static dmpc_err plain_prepare(dmpc_handle* h, KParams* P) {
   const int team = h->team;
@@ -543,10 +567,14 @@ static dmpc_err plain_prepare(dmpc_handle* h, KParams* P) {
   }
   if (!h->plain_st) {
     if (cudaMalloc(&h->plain_st, sizeof(PlainState) * h->batch) != cudaSuccess ||
-        cudaMalloc(&h->plain_dcount, sizeof(int)) != cudaSuccess ||
-        cudaHostAlloc(&h->plain_hcount, sizeof(int), cudaHostAllocDefault) != cudaSuccess)
+        cudaMalloc(&h->plain_params, sizeof(KParams)) != cudaSuccess)
       return fail(h, DMPC_E_OOM, "plain-form state allocation failed");
     cudaMemsetAsync(h->plain_st, 0, sizeof(PlainState) * h->batch, h->stream);
+  }
+  if (!h->plain_cap[0]) {
+    for (int i = 0; i < 2; ++i)
+      if (cudaStreamCreateWithFlags(&h->plain_cap[i], cudaStreamNonBlocking) != cudaSuccess)
+        return fail(h, DMPC_E_CUDA, "plain-form capture stream creation failed");
   }
   if (!h->plain_fn) return fail(h, DMPC_E_UNSUPPORTED, "no plain-form kernel for this batch");
   P->gws = h->plain_ws;
@@ -556,22 +584,101 @@ static dmpc_err plain_prepare(dmpc_handle* h, KParams* P) {
   return DMPC_OK;
 }
 
-static dmpc_err plain_pcg(dmpc_handle* h, const KParams& P) {
-  auto L = [&](int step) { return h->plain_fn(P, h->plain_st, step, 0, P.n_work, h->team, h->stream); };
-  const int maxit = h->opt.pcg_max_iters;
-  for (int base = 0; base < maxit; base += kPlainPoll) {
-    for (int j = 0; j < kPlainPoll; ++j) {
-      if (L(PS_MATVEC) != cudaSuccess || L(PS_AXPY) != cudaSuccess || L(PS_PRECAPPLY) != cudaSuccess ||
-          L(PS_BETA) != cudaSuccess)
-        return fail(h, DMPC_E_CUDA, "plain PCG launch failed");
-    }
-    plain_count_active<<<1, 256, 0, h->stream>>>(h->plain_st, P.order == h->d_order ? nullptr : P.order, P.n_work,
-                                                  h->plain_dcount);
-    cudaMemcpyAsync(h->plain_hcount, h->plain_dcount, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-    cudaError_t e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "plain PCG poll");
-    if (*h->plain_hcount == 0) break;
+// Capture one PCG solve as a conditional WHILE node on the capture stream cs (its body captured
+// on cb).  The condition starts at 1 on every launch; the body's last kernel sets it.
+static cudaError_t capture_pcg_loop(dmpc_handle* h, cudaStream_t cs, cudaStream_t cb, int grid) {
+  cudaStreamCaptureStatus status;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, &deps, nullptr, &ndeps);
+  if (e != cudaSuccess) return e;
+  if (status != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphConditionalHandle cond;
+  e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  for (int u = 0; u < kPlainUnroll && e == cudaSuccess; ++u)
+    for (int step : {PS_MATVEC, PS_AXPY, PS_PRECAPPLY, PS_BETA})
+      if (e == cudaSuccess) e = h->plain_fn(h->plain_params, h->plain_st, step, 0, grid, h->team, cb);
+  if (e == cudaSuccess) {
+    plain_pcg_continue<<<1, 256, 0, cb>>>(h->plain_st, h->plain_params, cond);
+    e = cudaGetLastError();
   }
+  cudaGraph_t out = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cb, &out);
+  return e != cudaSuccess ? e : e2;
+}
+
+// The graph of a forward solve (which = 0: load, per SQP iteration linearise / Schur /
+// preconditioner / PCG setup / PCG loop / finish / recovery / line search, outputs) or of a vjp
+// (which = 1), built on first use and rebuilt when the tiling changed.
+static dmpc_err plain_graph(dmpc_handle* h, int which, cudaGraphExec_t* out) {
+  if (h->plain_graph[which] && h->plain_graph_fn[which] == h->plain_fn && h->plain_graph_team[which] == h->team) {
+    *out = h->plain_graph[which];
+    return DMPC_OK;
+  }
+  if (h->plain_graph[which]) cudaGraphExecDestroy(h->plain_graph[which]);
+  h->plain_graph[which] = nullptr;
+  cudaStream_t cs = h->plain_cap[0], cb = h->plain_cap[1];
+  const int grid = h->batch;  // blocks beyond the solve's work list return at once
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(h, e, "plain-form graph capture");
+  auto L = [&](int step, int s_iter) {
+    if (e == cudaSuccess) e = h->plain_fn(h->plain_params, h->plain_st, step, s_iter, grid, h->team, cs);
+  };
+  auto loop = [&]() {
+    if (e == cudaSuccess) e = capture_pcg_loop(h, cs, cb, grid);
+  };
+  if (which == 0) {
+    L(PS_LOAD, 0);
+    for (int s_iter = 0; s_iter < h->opt.sqp_iters; ++s_iter) {
+      L(PS_LIN, s_iter); L(PS_SCHUR, s_iter); L(PS_PREC, s_iter); L(PS_PCG_SETUP, s_iter);
+      loop();
+      L(PS_PCG_FINISH, s_iter); L(PS_RECOVER, s_iter); L(PS_LS, s_iter);
+    }
+    L(PS_FWD_OUT, 0);
+  } else {
+    L(PS_LOAD, 0); L(PS_LIN, 0); L(PS_SCHUR, 0); L(PS_PREC, 0); L(PS_PCG_SETUP, 0);
+    loop();
+    L(PS_PCG_FINISH, 0); L(PS_BWD_FINISH, 0);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->plain_graph[which], g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->plain_graph[which] = nullptr;
+    cudaGetLastError();
+    return cuda_fail(h, e, "plain-form graph build");
+  }
+  h->plain_graph_fn[which] = h->plain_fn;
+  h->plain_graph_team[which] = h->team;
+  *out = h->plain_graph[which];
+  return DMPC_OK;
+}
+
+// Write the launch parameters to the device and launch the forward (0) or vjp (1) graph on the
+// handle's stream.  Asynchronous.
+static dmpc_err plain_launch(dmpc_handle* h, const KParams& P, int which) {
+  cudaGraphExec_t exec = nullptr;
+  dmpc_err er = plain_graph(h, which, &exec);
+  if (er != DMPC_OK) return er;
+  cudaError_t e = cudaMemcpyAsync(h->plain_params, &P, sizeof(KParams), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "plain-form graph launch");
   return DMPC_OK;
 }
 
@@ -602,18 +709,8 @@ extern "C" dmpc_err dmpc_solve_plain(dmpc_handle* h, const float* x_s, const flo
   P.res_z = h->res_z; P.res_lam = h->res_lam;
   P.res_xs = h->res_xs; P.res_th = h->res_th; P.res_xref = h->res_xref;
   P.status = status_out; P.pcg_iters = pcg_iters_out; P.alpha_hist = alpha_out;
-  auto L = [&](int step, int s) { return h->plain_fn(P, h->plain_st, step, s, h->batch, h->team, h->stream); };
-  if (L(PS_LOAD, 0) != cudaSuccess) return fail(h, DMPC_E_CUDA, "plain launch failed");
-  for (int s = 0; s < h->opt.sqp_iters; ++s) {
-    if (L(PS_LIN, s) != cudaSuccess || L(PS_SCHUR, s) != cudaSuccess || L(PS_PREC, s) != cudaSuccess ||
-        L(PS_PCG_SETUP, s) != cudaSuccess)
-      return fail(h, DMPC_E_CUDA, "plain launch failed");
-    er = plain_pcg(h, P);
-    if (er != DMPC_OK) return er;
-    if (L(PS_PCG_FINISH, s) != cudaSuccess || L(PS_RECOVER, s) != cudaSuccess || L(PS_LS, s) != cudaSuccess)
-      return fail(h, DMPC_E_CUDA, "plain launch failed");
-  }
-  if (L(PS_FWD_OUT, 0) != cudaSuccess) return fail(h, DMPC_E_CUDA, "plain launch failed");
+  er = plain_launch(h, P, 0);
+  if (er != DMPC_OK) return er;
   h->have_solution = true;
   h->have_store = false;
   h->last_had_xref = x_ref != nullptr;
@@ -641,17 +738,9 @@ extern "C" dmpc_err dmpc_vjp_plain(dmpc_handle* h, const float* dl_dz, float* dl
   P.lamt_init = (h->opt.warm_start && h->have_lamt) ? h->res_lamt : nullptr;
   P.res_lamt = h->res_lamt;
   P.dl_dtheta = dl_dtheta; P.dl_dxs = dl_dxs; P.lamt_out = lamt_out;
-  P.status = status_out; P.pcg_iters = nullptr;
-  auto L = [&](int step) { return h->plain_fn(P, h->plain_st, step, 0, h->batch, h->team, h->stream); };
-  if (L(PS_LOAD) != cudaSuccess || L(PS_LIN) != cudaSuccess || L(PS_SCHUR) != cudaSuccess ||
-      L(PS_PREC) != cudaSuccess || L(PS_PCG_SETUP) != cudaSuccess)
-    return fail(h, DMPC_E_CUDA, "plain launch failed");
-  er = plain_pcg(h, P);
+  P.status = status_out; P.pcg_iters = pcg_iters_out;   // written by the backward's last step only
+  er = plain_launch(h, P, 1);
   if (er != DMPC_OK) return er;
-  P.pcg_iters = pcg_iters_out;
-  auto L2 = [&](int step) { return h->plain_fn(P, h->plain_st, step, 0, h->batch, h->team, h->stream); };
-  if (L2(PS_PCG_FINISH) != cudaSuccess || L2(PS_BWD_FINISH) != cudaSuccess)
-    return fail(h, DMPC_E_CUDA, "plain launch failed");
   h->have_lamt = true;
   return DMPC_OK;
 }
@@ -765,18 +854,8 @@ extern "C" dmpc_err dmpc_solve_subset_plain(dmpc_handle* h, const int* index, in
   er = plain_prepare(h, &P);
   if (er != DMPC_OK) return er;
   P.lam_out = lam_out; P.status = status_out; P.pcg_iters = pcg_iters_out; P.alpha_hist = alpha_out;
-  auto L = [&](int step, int s) { return h->plain_fn(P, h->plain_st, step, s, n, h->team, h->stream); };
-  if (L(PS_LOAD, 0) != cudaSuccess) return fail(h, DMPC_E_CUDA, "plain launch failed");
-  for (int s = 0; s < h->opt.sqp_iters; ++s) {
-    if (L(PS_LIN, s) != cudaSuccess || L(PS_SCHUR, s) != cudaSuccess || L(PS_PREC, s) != cudaSuccess ||
-        L(PS_PCG_SETUP, s) != cudaSuccess)
-      return fail(h, DMPC_E_CUDA, "plain launch failed");
-    er = plain_pcg(h, P);
-    if (er != DMPC_OK) return er;
-    if (L(PS_PCG_FINISH, s) != cudaSuccess || L(PS_RECOVER, s) != cudaSuccess || L(PS_LS, s) != cudaSuccess)
-      return fail(h, DMPC_E_CUDA, "plain launch failed");
-  }
-  if (L(PS_FWD_OUT, 0) != cudaSuccess) return fail(h, DMPC_E_CUDA, "plain launch failed");
+  er = plain_launch(h, P, 0);
+  if (er != DMPC_OK) return er;
   h->have_solution = true;
   h->last_had_xref = x_ref != nullptr;
   return DMPC_OK;
@@ -785,7 +864,8 @@ extern "C" dmpc_err dmpc_solve_subset_plain(dmpc_handle* h, const int* index, in
 extern "C" long long dmpc_device_bytes(const dmpc_handle* h) {
   if (!h) return -1;
   long long b = (long long)h->bytes + (long long)h->gws_floats * (long long)sizeof(float);
-  if (h->plain_ws) b += (long long)h->plain_ws_floats * h->batch * (long long)sizeof(float) + (long long)sizeof(PlainState) * h->batch;
+  if (h->plain_ws) b += (long long)h->plain_ws_floats * h->batch * (long long)sizeof(float) +
+                       (long long)sizeof(PlainState) * h->batch + (long long)sizeof(KParams);
   return b;
 }
 
@@ -865,8 +945,11 @@ extern "C" void dmpc_destroy(dmpc_handle* h) {
   cudaFree(h->d_upd_idx);
   cudaFree(h->plain_ws);
   cudaFree(h->plain_st);
-  cudaFree(h->plain_dcount);
-  if (h->plain_hcount) cudaFreeHost(h->plain_hcount);
+  cudaFree(h->plain_params);
+  for (int i = 0; i < 2; ++i) {
+    if (h->plain_graph[i]) cudaGraphExecDestroy(h->plain_graph[i]);
+    if (h->plain_cap[i]) cudaStreamDestroy(h->plain_cap[i]);
+  }
   delete h;
 }
 

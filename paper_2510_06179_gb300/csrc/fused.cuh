@@ -14,6 +14,7 @@
 // side from (dl/dz, 0) (Eq. 7), the same PCG, z~ (Eq. 11 form), and
 // dl/dtheta = -(dF/dtheta)^T [z~; lambda~] (Eq. 3) contracted per knot.
 //
+// The A array holds A_t + I (see stage_linearise).
 // Data layout in the workspace: element e of knot k of an array lives at arr[e * KP + k]
 // (knot-minor), so the threads of a warp, which own consecutive knots, touch consecutive
 // words.  Thread `lane` of the team owns knots lane, lane + TEAM, ...; knot k holds x_k,
@@ -311,6 +312,11 @@ __device__ __noinline__ void stage_load(Ctx<M, TEAM>& c, bool use_z_init) {
 }
 
 // a1: linearise dynamics step t = k-1 at knot slot k (FP32): A_t, B_t, C_t, f_t; f_0 = x_0 - x_s.
+// The A array holds A_t + I, not A_t: for an integrator step A_t = -dPhi/dx = -I - d(Phi - x)/dx, and
+// in FP32 the identity would round away most of the step's own Jacobian (about dt times the
+// dynamics' derivatives), which sets the QP solution's precision; every consumer subtracts the
+// identity in its own precision (exactly in the FP64 and double-float operators).  C_t and f_t
+// are formed from the increment Phi - x, so no term of the size of the state cancels.
 template <class M, int TEAM>
 __device__ __noinline__ void stage_linearise(Ctx<M, TEAM>& c) {
   constexpr int NX = M::NX, NU = M::NU, NZ = NX + NU;
@@ -335,7 +341,7 @@ __device__ __noinline__ void stage_linearise(Ctx<M, TEAM>& c) {
     for (int i = 0; i < NX; ++i) xt[i] = X[i * KP + t];
 #pragma unroll
     for (int i = 0; i < NU; ++i) ut[i] = U[i * KP + t];
-    float phi[NX];
+    float phi[NX], fres[NX];
     if constexpr (is_lq<M>::value) {
       const float* tk = P.theta + c.o.th_off + (long long)t * M::PK;
 #pragma unroll
@@ -345,7 +351,7 @@ __device__ __noinline__ void stage_linearise(Ctx<M, TEAM>& c) {
         for (int j = 0; j < NX; ++j) {
           float a = tk[i * NX + j];
           acc = fmaf(a, xt[j], acc);
-          A[(i * NX + j) * KP + k] = -a;
+          A[(i * NX + j) * KP + k] = (i == j ? 1.f : 0.f) - a;   // A_t + I = I - Abar_t (exact)
         }
 #pragma unroll
         for (int j = 0; j < NU; ++j) {
@@ -356,6 +362,8 @@ __device__ __noinline__ void stage_linearise(Ctx<M, TEAM>& c) {
         phi[i] = acc;
         C[i * KP + k] = tk[NX * NX + NX * NU + i];
       }
+#pragma unroll
+      for (int i = 0; i < NX; ++i) fres[i] = X[i * KP + k] - phi[i];
     } else if constexpr (is_implicit<M>::value) {
       // trapezoidal rule: f = x_{t+1} - x_t - dt/2 (F(x_t, u_t) + F(x_{t+1}, u_t)), so
       // A = -I - dt/2 F_x(x_t), B = -dt/2 (F_u(x_t) + F_u(x_{t+1})), A^+ = I - dt/2 F_x(x_{t+1})
@@ -393,15 +401,16 @@ __device__ __noinline__ void stage_linearise(Ctx<M, TEAM>& c) {
       const float h = 0.5f * c.dt;
 #pragma unroll
       for (int i = 0; i < NX; ++i) {
-        phi[i] = xt[i] + h * fsum[i];  // so that f = x_{t+1} - phi below
-        float acc = 0.f;                // A^+ x_{t+1} + A x_t + B u_t
+        // C = A^+ x_{t+1} + A x_t + B u_t - f with A = -I + E, A^+ = I + E^+ and
+        // f = x_{t+1} - x_t - h (F_a + F_b):  C = E x_t + E^+ x_{t+1} + B u_t + h (F_a + F_b)
+        float acc = h * fsum[i];
 #pragma unroll
         for (int j = 0; j < NX; ++j) {
-          const float a = (i == j ? -1.f : 0.f) - h * ja[i * NZ + j];
-          const float ap = (i == j ? 1.f : 0.f) - h * jb[i * NZ + j];
-          A[(i * NX + j) * KP + k] = a;
-          Ap[(i * NX + j) * KP + k] = ap;
-          acc = fmaf(a, xt[j], fmaf(ap, xn[j], acc));
+          const float e = -h * ja[i * NZ + j];     // A + I
+          const float ep = -h * jb[i * NZ + j];    // A^+ - I
+          A[(i * NX + j) * KP + k] = e;
+          Ap[(i * NX + j) * KP + k] = (i == j ? 1.f : 0.f) + ep;
+          acc = fmaf(e, xt[j], fmaf(ep, xn[j], acc));
         }
 #pragma unroll
         for (int j = 0; j < NU; ++j) {
@@ -409,7 +418,8 @@ __device__ __noinline__ void stage_linearise(Ctx<M, TEAM>& c) {
           Bm[(i * NU + j) * KP + k] = b;
           acc = fmaf(b, ut[j], acc);
         }
-        C[i * KP + k] = acc - (xn[i] - phi[i]);
+        C[i * KP + k] = acc;
+        fres[i] = (xn[i] - xt[i]) - h * fsum[i];
       }
     } else {
       constexpr int CH = NZ <= 8 ? NZ : 8;
@@ -428,7 +438,7 @@ __device__ __noinline__ void stage_linearise(Ctx<M, TEAM>& c) {
         for (int i = 0; i < NU; ++i) ud[i] = Dual<CH>::seed(ut[i], NX + i - c0);
 #pragma unroll
         for (int j = 0; j < M::NP; ++j) pd[j] = Dual<CH>(pv[j]);
-        model_step<M>(xd, ud, pd, c.dt, out);
+        model_increment<M>(xd, ud, pd, c.dt, out);   // d = Phi - x and its derivatives
 #pragma unroll
         for (int i = 0; i < NX; ++i) {
           phi[i] = out[i].v;
@@ -438,7 +448,7 @@ __device__ __noinline__ void stage_linearise(Ctx<M, TEAM>& c) {
             if (col < NZ) {
               const float jv = out[i].d[q];
               if (col < NX) {
-                A[(i * NX + col) * KP + k] = -jv;
+                A[(i * NX + col) * KP + k] = -jv;    // A_t + I = -dd/dx
                 cacc[i] = fmaf(jv, xt[col], cacc[i]);
               } else {
                 Bm[(i * NU + (col - NX)) * KP + k] = -jv;
@@ -448,12 +458,16 @@ __device__ __noinline__ void stage_linearise(Ctx<M, TEAM>& c) {
           }
         }
       }
-      // C_t = A^+ x_{t+1} + A_t x_t + B_t u_t - f_t = Phi - J_x x_t - J_u u_t
+      // C_t = A^+ x_{t+1} + A_t x_t + B_t u_t - f_t = Phi - J_x x_t - J_u u_t = d - (dd/dx) x_t - (dd/du) u_t,
+      // f_t = x_{t+1} - Phi = (x_{t+1} - x_t) - d
 #pragma unroll
-      for (int i = 0; i < NX; ++i) C[i * KP + k] = phi[i] - cacc[i];
+      for (int i = 0; i < NX; ++i) {
+        C[i * KP + k] = phi[i] - cacc[i];
+        fres[i] = (X[i * KP + k] - xt[i]) - phi[i];
+      }
     }
 #pragma unroll
-    for (int i = 0; i < NX; ++i) Fv[i * KP + k] = X[i * KP + k] - phi[i];
+    for (int i = 0; i < NX; ++i) Fv[i * KP + k] = fres[i];
   }
   c.tm.sync();
 }
@@ -541,6 +555,8 @@ __device__ __noinline__ void stage_riccati_exact(Ctx<M, TEAM>& c) {
   float* UT = c.F(c.L.up);
   const int ln = c.tm.lane;
   auto slot = [&](int e, int k) -> double& { return W[e * KP + k]; };
+  // entry (i, j) of A_k (dynamics step k, knot slot k + 1) from the stored A_k + I
+  auto a_true = [&](int i, int j, int kn) -> double { return (double)A[(i * NX + j) * KP + kn] - (i == j ? 1.0 : 0.0); };
   // P_T, s_T (slot T)
   for (int e = ln; e < NX * NX; e += TEAM) {
     const int i = e / NX, j = e % NX;
@@ -555,10 +571,10 @@ __device__ __noinline__ void stage_riccati_exact(Ctx<M, TEAM>& c) {
       const int a = e / NZ, b = e % NZ;
       double acc = W[e * KP + k];
       for (int i = 0; i < NX; ++i) {
-        const double mi = -(double)(a < NX ? A[(i * NX + a) * KP + kn] : Bm[(i * NU + a - NX) * KP + kn]);
+        const double mi = -(a < NX ? a_true(i, a, kn) : (double)Bm[(i * NU + a - NX) * KP + kn]);
         double pj = 0.0;
         for (int j = 0; j < NX; ++j) {
-          const double mj = -(double)(b < NX ? A[(j * NX + b) * KP + kn] : Bm[(j * NU + b - NX) * KP + kn]);
+          const double mj = -(b < NX ? a_true(j, b, kn) : (double)Bm[(j * NU + b - NX) * KP + kn]);
           pj += slot(OP + i * NX + j, kn) * mj;
         }
         acc += mi * pj;
@@ -568,7 +584,7 @@ __device__ __noinline__ void stage_riccati_exact(Ctx<M, TEAM>& c) {
     for (int a = ln; a < NZ; a += TEAM) {
       double acc = -(double)g[(long long)k * NZ + a];
       for (int i = 0; i < NX; ++i)
-        acc += -(double)(a < NX ? A[(i * NX + a) * KP + kn] : Bm[(i * NU + a - NX) * KP + kn]) * slot(OS + i, kn);
+        acc += -(a < NX ? a_true(i, a, kn) : (double)Bm[(i * NU + a - NX) * KP + kn]) * slot(OS + i, kn);
       q[a] = acc;
     }
     c.tm.sync();
@@ -641,7 +657,7 @@ __device__ __noinline__ void stage_riccati_exact(Ctx<M, TEAM>& c) {
       for (int i = 0; i < NX; ++i) {
         double acc = 0.0;
 #pragma unroll
-        for (int j = 0; j < NX; ++j) acc -= (double)A[(i * NX + j) * KP + k + 1] * x[j];
+        for (int j = 0; j < NX; ++j) acc -= a_true(i, j, k + 1) * x[j];
 #pragma unroll
         for (int a = 0; a < NU; ++a) acc -= (double)Bm[(i * NU + a) * KP + k + 1] * u[a];
         xn[i] = acc;
@@ -704,7 +720,9 @@ __device__ __noinline__ void stage_schur(Ctx<M, TEAM>& c, bool rhs_from_qp) {
           float sum = 0.f;
 #pragma unroll
           for (int l = 0; l < NX; ++l) {
-            sum = fmaf(A[(i * NX + l) * KP + k] * qt[l], A[(j * NX + l) * KP + k], sum);
+            const float ail = A[(i * NX + l) * KP + k] - (i == l ? 1.f : 0.f);
+            const float ajl = A[(j * NX + l) * KP + k] - (j == l ? 1.f : 0.f);
+            sum = fmaf(ail * qt[l], ajl, sum);
             sum = fmaf(Ap[(i * NX + l) * KP + k] * qi[l], Ap[(j * NX + l) * KP + k], sum);
           }
 #pragma unroll
@@ -718,7 +736,7 @@ __device__ __noinline__ void stage_schur(Ctx<M, TEAM>& c, bool rhs_from_qp) {
 #pragma unroll
           for (int l = 0; l < NX; ++l) {
             const float apv = (t == 0) ? (j == l ? 1.f : 0.f) : Ap[(j * NX + l) * KP + t];
-            sum = fmaf(A[(i * NX + l) * KP + k] * qt[l], apv, sum);
+            sum = fmaf((A[(i * NX + l) * KP + k] - (i == l ? 1.f : 0.f)) * qt[l], apv, sum);
           }
           O[(i * NX + j) * KP + k] = sum;
         }
@@ -737,7 +755,8 @@ __device__ __noinline__ void stage_schur(Ctx<M, TEAM>& c, bool rhs_from_qp) {
           double z = 0.0;
 #pragma unroll
           for (int j = 0; j < NX; ++j)
-            z += (double)A[(i * NX + j) * KP + k] * vq[j] + (double)Ap[(i * NX + j) * KP + k] * vk[j];
+            z += ((double)A[(i * NX + j) * KP + k] - (i == j ? 1.0 : 0.0)) * vq[j] +
+                 (double)Ap[(i * NX + j) * KP + k] * vk[j];
 #pragma unroll
           for (int j = 0; j < NU; ++j) z += (double)Bm[(i * NU + j) * KP + k] * vr[j];
           G[i * KP + k] = -(double)C[i * KP + k] - z;
@@ -750,9 +769,9 @@ __device__ __noinline__ void stage_schur(Ctx<M, TEAM>& c, bool rhs_from_qp) {
     for (int i = 0; i < NX; ++i) qt[i] = 1.f / c.qproj(t, i);
 #pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NU; ++i) ri[i] = 1.f / c.misc(MS_RP + i);
-    float a[NX * NX], b[NX * NU];
+    float a[NX * NX], b[NX * NU];   // a: A_t in FP32 (the stored A_t + I minus the identity)
 #pragma unroll (NX <= 8 ? 32 : 1)
-    for (int i = 0; i < NX * NX; ++i) a[i] = A[i * KP + k];
+    for (int i = 0; i < NX * NX; ++i) a[i] = A[i * KP + k] - ((i / NX) == (i % NX) ? 1.f : 0.f);
 #pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NX * NU; ++i) b[i] = Bm[i * KP + k];
 #pragma unroll (NX <= 8 ? 32 : 1)
@@ -778,9 +797,9 @@ __device__ __noinline__ void stage_schur(Ctx<M, TEAM>& c, bool rhs_from_qp) {
       for (int j = 0; j < NU; ++j) vr[j] = c.rlin(j, U[j * KP + t]) * c.rinv(j);
 #pragma unroll (NX <= 8 ? 32 : 1)
       for (int i = 0; i < NX; ++i) {
-        double z = c.qlin(k, i, X[i * KP + k]) * c.qinv(k, i);
+        double z = c.qlin(k, i, X[i * KP + k]) * c.qinv(k, i) - vq[i];
 #pragma unroll (NX <= 8 ? 32 : 1)
-        for (int j = 0; j < NX; ++j) z += (double)a[i * NX + j] * vq[j];
+        for (int j = 0; j < NX; ++j) z += (double)A[(i * NX + j) * KP + k] * vq[j];   // exact A_t + I
 #pragma unroll (NX <= 8 ? 32 : 1)
         for (int j = 0; j < NU; ++j) z += (double)b[i * NU + j] * vr[j];
         G[i * KP + k] = -(double)C[i * KP + k] - z;
@@ -872,10 +891,10 @@ __device__ __noinline__ void hp_apply(Ctx<M, TEAM>& c, const double* src, bool r
       double ln[NX];
 #pragma unroll
       for (int j = 0; j < NX; ++j) ln[j] = src[j * KP + k + 1];
-      // A_k lives at slot k + 1
+      // A_k lives at slot k + 1 (stored as A_k + I)
 #pragma unroll
       for (int i = 0; i < NX; ++i) {
-        double s = wx[i];
+        double s = wx[i] - ln[i];
 #pragma unroll
         for (int j = 0; j < NX; ++j) s += (double)A[(j * NX + i) * KP + k + 1] * ln[j];
         wx[i] = s;
@@ -924,7 +943,7 @@ __device__ __noinline__ void hp_apply(Ctx<M, TEAM>& c, const double* src, bool r
       c.ginv(t, wx, wu, vx, vu);
 #pragma unroll
       for (int i = 0; i < NX; ++i) {
-        double acc = s[i];
+        double acc = s[i] - vx[i];
 #pragma unroll
         for (int j = 0; j < NX; ++j) acc += (double)A[(i * NX + j) * KP + k] * vx[j];
 #pragma unroll
@@ -996,9 +1015,10 @@ __device__ __noinline__ void df_apply(Ctx<M, TEAM>& c, const dfl* v, dfl* out, d
       } else {
         dacc_add(a, v[i * KP + k]);
       }
-      if (k < T) {
+      if (k < T) {   // (A_k + I)^T v_{k+1} - v_{k+1}
 #pragma unroll
         for (int j = 0; j < NX; ++j) dacc_fma(a, A[(j * NX + i) * KP + k + 1], v[j * KP + k + 1]);
+        dacc_add(a, df_neg(v[i * KP + k + 1]));
       }
       WX[i * KP + k] = dacc_get(a);
     }
@@ -1038,6 +1058,7 @@ __device__ __noinline__ void df_apply(Ctx<M, TEAM>& c, const dfl* v, dfl* out, d
       if (k > 0) {
 #pragma unroll
         for (int j = 0; j < NX; ++j) dacc_fma(a, A[(i * NX + j) * KP + k], vx[j]);
+        dacc_add(a, df_neg(vx[i]));
 #pragma unroll
         for (int j = 0; j < NU; ++j) dacc_fma(a, Bm[(i * NU + j) * KP + k], vu[j]);
       }
@@ -1583,8 +1604,10 @@ template <class M, int KPL>
 __device__ __forceinline__ void warp_S_df(const float (&Ak)[KPL][M::NX * M::NX], const float (&Bk)[KPL][M::NX * M::NU],
                                           const float (&Apk)[KPL][M::NX * M::NX],
                                           const dfl (&qi)[KPL][M::NX], const dfl (&ri)[M::NU], const bool (&has_u)[KPL],
-                                          const dfl (&v)[KPL][M::NX], dfl (&out)[KPL][M::NX], int ln) {
-  // Apk: A^+ of the lane's knots (identity at knot 0); read only for implicit integrators
+                                          const bool (&has_a)[KPL], const dfl (&v)[KPL][M::NX], dfl (&out)[KPL][M::NX],
+                                          int ln) {
+  // Ak: A_k + I of the knots that carry a dynamics row (has_a), else 0; Apk: A^+ of the lane's
+  // knots (identity at knot 0), read only for implicit integrators
   constexpr int NX = M::NX, NU = M::NU;
   // pass 1: w = H^T v.  Knot k+1 owns A_k (slot k+1) and sends A_k^T v_{k+1}, B_k^T v_{k+1}.
   dfl t[KPL][NX], ub[KPL][NU];
@@ -1595,6 +1618,7 @@ __device__ __forceinline__ void warp_S_df(const float (&Ak)[KPL][M::NX * M::NX],
       dacc a = dacc_zero();
 #pragma unroll
       for (int i = 0; i < NX; ++i) dacc_fma(a, Ak[j][i * NX + b], v[j][i]);
+      if (has_a[j]) dacc_add(a, df_neg(v[j][b]));
       t[j][b] = dacc_get(a);
     }
 #pragma unroll
@@ -1666,6 +1690,7 @@ __device__ __forceinline__ void warp_S_df(const float (&Ak)[KPL][M::NX * M::NX],
       }
 #pragma unroll
       for (int q = 0; q < NX; ++q) dacc_fma(a, Ak[j][i * NX + q], (j > 0) ? vx[j > 0 ? j - 1 : 0][q] : vxm[q]);
+      if (has_a[j]) dacc_add(a, df_neg((j > 0) ? vx[j > 0 ? j - 1 : 0][i] : vxm[i]));
 #pragma unroll
       for (int q = 0; q < NU; ++q) dacc_fma(a, Bk[j][i * NU + q], (j > 0) ? vu[j > 0 ? j - 1 : 0][q] : vum[q]);
       out[j][i] = dacc_get(a);
@@ -1682,12 +1707,13 @@ __device__ __noinline__ int stage_pcg_warp_df(Ctx<M, 32>& c, float eta0f, int ma
   const double* G = c.Dp(c.L.d_gam);
   float Pdk[KPL][NX * NX], Pok[KPL][NX * NX], Ak[KPL][NX * NX], Bk[KPL][NX * NU], Apk[KPL][NX * NX];
   dfl qi[KPL][NX], ri[NU];
-  bool live[KPL], has_u[KPL];
+  bool live[KPL], has_u[KPL], has_a[KPL];
 #pragma unroll
   for (int j = 0; j < KPL; ++j) {
     const int k = ln * KPL + j;
     live[j] = k < K;
     has_u[j] = k < T;
+    has_a[j] = live[j] && k > 0;
 #pragma unroll
     for (int a = 0; a < NX; ++a)
 #pragma unroll
@@ -1724,7 +1750,7 @@ __device__ __noinline__ int stage_pcg_warp_df(Ctx<M, 32>& c, float eta0f, int ma
 #pragma unroll
     for (int i = 0; i < NX; ++i) x[j][i] = live[j] ? df_from(LP[i * KP + ln * KPL + j]) : df_make(0.f);
   // r = gamma - S x, z = Phi^-1 r, p = z, eta = r^T z
-  warp_S_df<M, KPL>(Ak, Bk, Apk, qi, ri, has_u, x, y, ln);
+  warp_S_df<M, KPL>(Ak, Bk, Apk, qi, ri, has_u, has_a, x, y, ln);
 #pragma unroll
   for (int j = 0; j < KPL; ++j)
 #pragma unroll
@@ -1739,7 +1765,7 @@ __device__ __noinline__ int stage_pcg_warp_df(Ctx<M, 32>& c, float eta0f, int ma
   int it = 0;
   bool converged = !(eta.hi > thr.hi);
   while (!converged && it < maxit) {
-    warp_S_df<M, KPL>(Ak, Bk, Apk, qi, ri, has_u, p, y, ln);
+    warp_S_df<M, KPL>(Ak, Bk, Apk, qi, ri, has_u, has_a, p, y, ln);
     dacc va = dacc_zero();
 #pragma unroll
     for (int j = 0; j < KPL; ++j)
@@ -1924,11 +1950,181 @@ __device__ __noinline__ int stage_pcg_warp(Ctx<M, 32>& c) {
   return it;
 }
 
+// a4, single-warp variant with ONE reduction per iteration (pcg_variant = 1): Algorithm 4
+// reorganised as Chronopoulos and Gear's conjugate gradient (1989).  In exact arithmetic it
+// produces the same iterates: with u = Phi^-1 r and w = S u, the two inner products
+// gamma = r^T u (Algorithm 4's eta) and delta = w^T u are formed together, beta = gamma / gamma_old,
+// alpha = gamma / (delta - beta gamma / alpha_old), p = u + beta p and s = w + beta s (s = S p by
+// recurrence), lambda += alpha p, r -= alpha s.  One fused warp reduction of two values replaces
+// Algorithm 4's two dependent reductions, which shortens the serial chain of an iteration; the two
+// block-tridiagonal products (Phi^-1 r, then S u) stay dependent.  Reliable updates, stagnation
+// test and double-float rescue as in stage_pcg_warp; at each true-residual replacement s is
+// recomputed as S p so the recurrence does not drift.
+template <class M, int KPL>
+__device__ __noinline__ int stage_pcg_warp_cg(Ctx<M, 32>& c) {
+  constexpr int NX = M::NX;
+  const KParams& P = *c.P;
+  const int K = c.K, KP = c.KP;
+  const int ln = c.tm.lane;
+  float* R = c.F(c.L.r);
+  double* LP = c.Dp(c.L.d_lamp);
+  const double* G = c.Dp(c.L.d_gam);
+  const float tol2 = P.opt.pcg_tol * P.opt.pcg_tol;
+  const float dl2 = P.opt.ru_delta * P.opt.ru_delta;
+  float Dk[KPL][NX * NX], Ok[KPL][NX * NX], Pdk[KPL][NX * NX], Pok[KPL][NX * NX];
+  bool live[KPL];
+#pragma unroll
+  for (int j = 0; j < KPL; ++j) {
+    const int k = ln * KPL + j;
+    live[j] = k < K;
+#pragma unroll
+    for (int e = 0; e < NX * NX; ++e) {
+      Dk[j][e] = live[j] ? c.F(c.L.D)[e * KP + k] : 0.f;
+      Ok[j][e] = (live[j] && k > 0) ? c.F(c.L.O)[e * KP + k] : 0.f;
+      Pdk[j][e] = live[j] ? c.F(c.L.Pd)[e * KP + k] : 0.f;
+      Pok[j][e] = (live[j] && k > 0) ? c.F(c.L.Po)[e * KP + k] : 0.f;
+    }
+  }
+  // eta_0 = gamma^T Phi^-1 gamma, from the FP32-rounded gamma
+  float r[KPL][NX], u[KPL][NX], w[KPL][NX], p[KPL][NX], sv[KPL][NX], dl[KPL][NX];
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) r[j][i] = live[j] ? (float)G[i * KP + ln * KPL + j] : 0.f;
+  warp_btmv<NX, KPL>(Pdk, Pok, r, u, ln);
+  float e0[1] = {0.f};
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) e0[0] = fmaf(r[j][i], u[j][i], e0[0]);
+  warp_sum(e0);
+  const float eta0 = e0[0];
+  if (P.opt.pcg_precision == 1) return stage_pcg_warp_df<M, KPL>(c, eta0, P.opt.pcg_max_iters);
+  // true residual of the initial guess; u = Phi^-1 r, w = S u, gamma = r^T u, delta = w^T u
+  hp_residual<M, 32>(c, LP);
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { r[j][i] = live[j] ? R[i * KP + ln * KPL + j] : 0.f; dl[j][i] = 0.f; }
+  warp_btmv<NX, KPL>(Pdk, Pok, r, u, ln);
+  warp_btmv<NX, KPL>(Dk, Ok, u, w, ln);
+  float gd[2] = {0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { gd[0] = fmaf(r[j][i], u[j][i], gd[0]); gd[1] = fmaf(w[j][i], u[j][i], gd[1]); }
+  warp_sum(gd);
+  float gam = gd[0];
+  float eta_ref = gam, eta_true = gam;
+  int it = 0, stall = 0;
+  bool converged = !(gam > tol2 * eta0);
+  bool folded = true;
+  const int maxit = P.opt.pcg_max_iters;
+  // first direction: p = u, s = w, alpha = gamma / delta
+  float alpha = __fdividef(gam, gd[1]);
+#pragma unroll
+  for (int j = 0; j < KPL; ++j)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) { p[j][i] = u[j][i]; sv[j][i] = w[j][i]; }
+  bool broke = !(gd[1] > 0.f) || !isfinite(gd[1]);
+  while (!converged && !broke && it < maxit) {
+#pragma unroll
+    for (int j = 0; j < KPL; ++j)
+#pragma unroll
+      for (int i = 0; i < NX; ++i) { dl[j][i] = fmaf(alpha, p[j][i], dl[j][i]); r[j][i] = fmaf(-alpha, sv[j][i], r[j][i]); }
+    folded = false;
+    warp_btmv<NX, KPL>(Pdk, Pok, r, u, ln);        // u = Phi^-1 r
+    warp_btmv<NX, KPL>(Dk, Ok, u, w, ln);          // w = S u
+    float q[2] = {0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < KPL; ++j)
+#pragma unroll
+      for (int i = 0; i < NX; ++i) { q[0] = fmaf(r[j][i], u[j][i], q[0]); q[1] = fmaf(w[j][i], u[j][i], q[1]); }
+    warp_sum(q);
+    float gam_new = q[0], del = q[1];
+    ++it;
+    bool recompute_s = false;
+    if (gam_new < dl2 * eta_ref || !(gam_new > tol2 * eta0) || it >= maxit || !isfinite(gam_new)) {
+      // reliable update: fold the FP32 correction into the FP64 solution, true residual
+#pragma unroll
+      for (int j = 0; j < KPL; ++j)
+        if (live[j])
+#pragma unroll
+          for (int i = 0; i < NX; ++i) { LP[i * KP + ln * KPL + j] += (double)dl[j][i]; dl[j][i] = 0.f; }
+      folded = true;
+      hp_residual<M, 32>(c, LP);
+#pragma unroll
+      for (int j = 0; j < KPL; ++j)
+#pragma unroll
+        for (int i = 0; i < NX; ++i) r[j][i] = live[j] ? R[i * KP + ln * KPL + j] : 0.f;
+      warp_btmv<NX, KPL>(Pdk, Pok, r, u, ln);
+      warp_btmv<NX, KPL>(Dk, Ok, u, w, ln);
+      float q2[2] = {0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < KPL; ++j)
+#pragma unroll
+        for (int i = 0; i < NX; ++i) { q2[0] = fmaf(r[j][i], u[j][i], q2[0]); q2[1] = fmaf(w[j][i], u[j][i], q2[1]); }
+      warp_sum(q2);
+      gam_new = q2[0];
+      del = q2[1];
+      eta_ref = gam_new;
+      if (!(gam_new > tol2 * eta0)) { converged = true; break; }
+      if (!isfinite(gam_new)) break;
+      if (gam_new > 0.25f * eta_true) {
+        if (++stall >= 2) break;
+      } else {
+        stall = 0;
+      }
+      eta_true = gam_new;
+      if (it >= maxit) break;
+      recompute_s = true;
+    }
+    const float beta = __fdividef(gam_new, gam);
+    const float den = del - beta * __fdividef(gam_new, alpha);
+    if (!(den > 0.f) || !isfinite(den)) break;
+    alpha = __fdividef(gam_new, den);
+    gam = gam_new;
+#pragma unroll
+    for (int j = 0; j < KPL; ++j)
+#pragma unroll
+      for (int i = 0; i < NX; ++i) { p[j][i] = fmaf(beta, p[j][i], u[j][i]); sv[j][i] = fmaf(beta, sv[j][i], w[j][i]); }
+    if (recompute_s) {
+      // s = S p exactly after a residual replacement, and alpha from it (Algorithm 4's form)
+      warp_btmv<NX, KPL>(Dk, Ok, p, sv, ln);
+      float v[1] = {0.f};
+#pragma unroll
+      for (int j = 0; j < KPL; ++j)
+#pragma unroll
+        for (int i = 0; i < NX; ++i) v[0] = fmaf(p[j][i], sv[j][i], v[0]);
+      warp_sum(v);
+      if (!(v[0] > 0.f) || !isfinite(v[0])) break;
+      alpha = __fdividef(gam, v[0]);
+    }
+  }
+  if (!folded) {
+#pragma unroll
+    for (int j = 0; j < KPL; ++j)
+      if (live[j])
+#pragma unroll
+        for (int i = 0; i < NX; ++i) LP[i * KP + ln * KPL + j] += (double)dl[j][i];
+    hp_residual<M, 32>(c, LP);
+  }
+  if (!converged) {
+    c.status |= ST_FP64_RESCUE;
+    it += stage_pcg_warp_df<M, KPL>(c, eta0, maxit);
+  }
+  return it;
+}
+
 // PCG entry: the register-resident inner loop when one knot per lane fits (nx <= 6).
 template <class M, int TEAM>
 __device__ __forceinline__ int run_pcg(Ctx<M, TEAM>& c) {
   if constexpr (M::NX <= 4) {
     if constexpr (TEAM == 32) {
+      if (c.P->opt.pcg_variant == 1) {
+        if (c.K <= 32) return stage_pcg_warp_cg<M, 1>(c);
+        if (c.K <= 64) return stage_pcg_warp_cg<M, 2>(c);
+      }
       if (c.K <= 32) return stage_pcg_warp<M, 1>(c);
       if (c.K <= 64) return stage_pcg_warp<M, 2>(c);
     } else {
@@ -2057,11 +2253,17 @@ __device__ __noinline__ float stage_linesearch(Ctx<M, TEAM>& c) {
             trap_residual<M>(xa, ua, xn, pv, c.dt, rr);
 #pragma unroll
             for (int i = 0; i < NX; ++i) g += fabs((double)rr[i]);
-          } else {
+          } else if constexpr (is_lq<M>::value) {
             plain_step<M>(tk, pv, c.dt, xa, ua, xn);
 #pragma unroll
             for (int i = 0; i < NX; ++i)
               g += fabs((double)(X[i * KP + k] + a * (XP[i * KP + k] - X[i * KP + k])) - (double)xn[i]);
+          } else {
+            // f_t = (x_{t+1} - x_t) - (Phi - x_t), the increment formed without adding x_t
+            model_increment<M>(xa, ua, pv, c.dt, xn);
+#pragma unroll
+            for (int i = 0; i < NX; ++i)
+              g += fabs((double)((X[i * KP + k] + a * (XP[i * KP + k] - X[i * KP + k])) - xa[i]) - (double)xn[i]);
           }
         }
         red[11 + j] += g;
@@ -2143,7 +2345,8 @@ __device__ __noinline__ void write_inspect(Ctx<M, TEAM>& c, int iters) {
   for (int k = c.tm.lane; k < K; k += TEAM) {
     if (k >= 1) {
       const int t = k - 1;
-      for (int e = 0; e < NX * NX; ++e) out[o + (long long)t * NX * NX + e] = c.F(c.L.A)[e * KP + k];
+      for (int e = 0; e < NX * NX; ++e)
+        out[o + (long long)t * NX * NX + e] = c.F(c.L.A)[e * KP + k] - ((e / NX) == (e % NX) ? 1.f : 0.f);
       for (int e = 0; e < NX * NU; ++e) out[o + (long long)T * NX * NX + (long long)t * NX * NU + e] = c.F(c.L.Bm)[e * KP + k];
       for (int e = 0; e < NX; ++e) out[o + (long long)T * (NX * NX + NX * NU) + (long long)t * NX + e] = c.F(c.L.C)[e * KP + k];
     }
@@ -2288,6 +2491,7 @@ __device__ __noinline__ void stage_bwd_rhs(Ctx<M, TEAM>& c) {
       c.ginv(t, gx, gu, vx, vu);
 #pragma unroll
       for (int i = 0; i < NX; ++i) {
+        s[i] -= vx[i];   // A_t = (stored A_t + I) - I
 #pragma unroll
         for (int j = 0; j < NX; ++j) s[i] += (double)A[(i * NX + j) * KP + k] * vx[j];
 #pragma unroll

@@ -8,8 +8,9 @@ namespace dmpc {
 typedef cudaError_t (*LaunchFn)(const KParams& P, int grid, int threads, size_t smem, cudaStream_t s);
 
 struct PlainState;
-// plain one-launch-per-step form: one launch = one step for the batch (grid = batch, block = team)
-typedef cudaError_t (*PlainFn)(const KParams& P, PlainState* st, int step, int s_iter, int grid, int threads,
+// plain one-launch-per-step form: one launch = one step for the batch (grid = batch, block = team);
+// P is a device pointer
+typedef cudaError_t (*PlainFn)(const KParams* P, PlainState* st, int step, int s_iter, int grid, int threads,
                                cudaStream_t s);
 
 struct KernelEntry {
@@ -30,10 +31,12 @@ struct KernelEntry {
   int DMPC_REGISTER_NAME(model, 128)(KernelEntry*); \
   int DMPC_REGISTER_NAME(model, 256)(KernelEntry*);
 DMPC_DECLARE_TEAMS(lq)
+DMPC_DECLARE_TEAMS(lq16)
 DMPC_DECLARE_TEAMS(pendulum)
 DMPC_DECLARE_TEAMS(cartpole)
 DMPC_DECLARE_TEAMS(bicycle)
 DMPC_DECLARE_TEAMS(single_track)
+DMPC_DECLARE_TEAMS(single_track_rate)
 DMPC_DECLARE_TEAMS(rigid_body)
 DMPC_DECLARE_TEAMS(attitude)
 DMPC_DECLARE_TEAMS(mixed)

@@ -18,7 +18,7 @@ cudaError_t launch_fused(const KParams& P, int grid, int threads, size_t smem, c
 }
 
 template <int TEAM, class... Ms>
-cudaError_t launch_plain(const KParams& P, PlainState* st, int step, int s_iter, int grid, int threads, cudaStream_t s) {
+cudaError_t launch_plain(const KParams* P, PlainState* st, int step, int s_iter, int grid, int threads, cudaStream_t s) {
   plain_kernel<TEAM, Ms...><<<grid, threads, 0, s>>>(P, st, step, s_iter);
   return cudaGetLastError();
 }

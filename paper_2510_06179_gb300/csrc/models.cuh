@@ -15,11 +15,12 @@ namespace dmpc {
 enum ModelId : int {
   M_LQ = 0, M_PENDULUM = 1, M_CARTPOLE = 2, M_KIN_BICYCLE = 3,
   M_SINGLE_TRACK = 4, M_RIGID_BODY12 = 5, M_ATTITUDE = 6,
+  M_SINGLE_TRACK_RATE = 7,
   // internal ids of the trapezoidal (implicit) variants: model id + kTrapIdOffset
   M_PENDULUM_TRAP = 17, M_CARTPOLE_TRAP = 18
 };
 constexpr int kTrapIdOffset = 16;
-enum Integrator : int { I_RK4 = 0, I_EULER = 1, I_AFFINE = 2, I_TRAP = 3 };
+enum Integrator : int { I_RK4 = 0, I_EULER = 1, I_AFFINE = 2, I_TRAP = 3, I_RATE = 4 };
 
 constexpr float kGravity = 9.81f;
 
@@ -145,9 +146,52 @@ struct Attitude {
   }
 };
 
+// The increment Phi(x, u; p) - x of one integrator step of model M, formed without adding x
+// (dt k1 for Euler, dt/6 (k1 + 2 k2 + 2 k3 + k4) for RK4): its value and derivatives are small
+// next to x, so they keep their FP32 precision where Phi itself would round them away.
+template <class M, class S>
+__device__ __forceinline__ void model_increment(const S* x, const S* u, const S* p, float dt, S* dx) {
+  if constexpr (M::INTEG == I_RATE) {
+    // control-rate augmentation: the base model's increment with the input held in the state,
+    // and dt times the rate for the input part
+    using Bm = typename M::Base;
+    model_increment<Bm>(x, x + Bm::NX, p, dt, dx);
+#pragma unroll
+    for (int i = 0; i < M::NU; ++i) dx[Bm::NX + i] = dt * u[i];
+    return;
+  } else if constexpr (M::INTEG == I_EULER) {
+    S k1[M::NX];
+    M::f(x, u, p, k1);
+#pragma unroll
+    for (int i = 0; i < M::NX; ++i) dx[i] = dt * k1[i];
+    return;
+  } else {
+  S k[M::NX], acc[M::NX], xt[M::NX];
+  M::f(x, u, p, k);
+#pragma unroll
+  for (int i = 0; i < M::NX; ++i) { acc[i] = k[i]; xt[i] = x[i] + (0.5f * dt) * k[i]; }
+  M::f(xt, u, p, k);
+#pragma unroll
+  for (int i = 0; i < M::NX; ++i) { acc[i] = acc[i] + 2.0f * k[i]; xt[i] = x[i] + (0.5f * dt) * k[i]; }
+  M::f(xt, u, p, k);
+#pragma unroll
+  for (int i = 0; i < M::NX; ++i) { acc[i] = acc[i] + 2.0f * k[i]; xt[i] = x[i] + dt * k[i]; }
+  M::f(xt, u, p, k);
+#pragma unroll
+  for (int i = 0; i < M::NX; ++i) dx[i] = (dt / 6.0f) * (acc[i] + k[i]);
+  }
+}
+
 // One integrator step Phi(x, u; p) of model M.
 template <class M, class S>
 __device__ __forceinline__ void model_step(const S* x, const S* u, const S* p, float dt, S* xn) {
+  if constexpr (M::INTEG == I_RATE) {
+    S dx[M::NX];
+    model_increment<M>(x, u, p, dt, dx);
+#pragma unroll
+    for (int i = 0; i < M::NX; ++i) xn[i] = x[i] + dx[i];
+    return;
+  } else {
   if (M::INTEG == I_EULER) {
     S k1[M::NX];
     M::f(x, u, p, k1);
@@ -168,7 +212,17 @@ __device__ __forceinline__ void model_step(const S* x, const S* u, const S* p, f
   M::f(xt, u, p, k);
 #pragma unroll
   for (int i = 0; i < M::NX; ++i) xn[i] = x[i] + (dt / 6.0f) * (acc[i] + k[i]);
+  }
 }
+
+// Control-rate augmentation of a base model (App. B.3): state (x, u), input u_dot, with
+// x_{t+1} = Phi_t(x_t, u_t) of the base model and u_{t+1} = u_t + dt u_dot_t, so the input cost
+// penalises the rate of the base model's input.  Same parameters as the base model.
+template <class B_, int ID_>
+struct Rate {
+  using Base = B_;
+  static constexpr int ID = ID_, NX = B_::NX + B_::NU, NU = B_::NU, NP = B_::NP, INTEG = I_RATE;
+};
 
 // A continuous model integrated by the implicit trapezoidal rule.
 template <class Base>

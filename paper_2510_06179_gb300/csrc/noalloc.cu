@@ -66,7 +66,8 @@ bool shape_ok(const dmpc_ocp_desc& d, int* p_shared) {
   int nx = -1, nu = -1, ps = 0;
   switch (d.model) {
     case DMPC_MODEL_LQ:
-      if (!((d.nx == 2 && d.nu == 1) || (d.nx == 3 && d.nu == 2) || (d.nx == 4 && d.nu == 1) || (d.nx == 8 && d.nu == 4)))
+      if (!((d.nx == 2 && d.nu == 1) || (d.nx == 3 && d.nu == 2) || (d.nx == 4 && d.nu == 1) || (d.nx == 8 && d.nu == 4) ||
+            (d.nx == 16 && d.nu == 8)))
         return false;
       nx = d.nx; nu = d.nu; ps = 0;
       break;
@@ -76,6 +77,7 @@ bool shape_ok(const dmpc_ocp_desc& d, int* p_shared) {
     case DMPC_MODEL_SINGLE_TRACK: nx = 6; nu = 2; ps = 2; break;
     case DMPC_MODEL_RIGID_BODY12: nx = 12; nu = 4; ps = 4; break;
     case DMPC_MODEL_ATTITUDE: nx = 3; nu = 3; ps = 3; break;
+    case DMPC_MODEL_SINGLE_TRACK_RATE: nx = 8; nu = 2; ps = 2; break;
     default: return false;
   }
   *p_shared = ps;
@@ -101,7 +103,7 @@ extern "C" dmpc_err dmpc_solve_noalloc(const dmpc_ocp_desc* desc, int batch, con
   if (o.sqp_iters < 1 || o.sqp_iters > 1000 || o.n_alpha < 1 || o.n_alpha > 8 || !(o.pcg_tol > 0.f) ||
       !(o.pcg_tol < 1.f) || o.pcg_max_iters < 1 || !(o.ru_delta > 0.f && o.ru_delta < 1.f) ||
       !(o.ls_eta > 0.f && o.ls_eta < 1.f) || !(o.feas_tol >= 0.f) || (o.pcg_precision != 0 && o.pcg_precision != 1) ||
-      (o.exact_hessian != 0 && o.exact_hessian != 1))
+      (o.exact_hessian != 0 && o.exact_hessian != 1) || (o.pcg_variant != 0 && o.pcg_variant != 1))
     return DMPC_E_ARG;
   for (int i = 0; i < o.n_alpha; ++i)
     if (!(o.alpha[i] > 0.f && o.alpha[i] <= 1.f)) return DMPC_E_ARG;
@@ -128,6 +130,18 @@ extern "C" dmpc_err dmpc_solve_noalloc(const dmpc_ocp_desc* desc, int batch, con
     else team = K <= 32 ? 32 : (K <= 64 ? 64 : (K <= 320 ? 128 : 256));
   }
   if (team != 32 && team != 64 && team != 128 && team != 256) return DMPC_E_ARG;
+  KernelEntry table[kMaxKernelEntries];
+  const int n_entries = collect_kernel_entries(table);
+  auto find = [&](int tm) -> LaunchFn {
+    for (int i = 0; i < n_entries; ++i)
+      if (table[i].team == tm && table[i].model == kmodel && table[i].nx == nx && table[i].nu == nu) return table[i].fn;
+    return nullptr;
+  };
+  if (o.team_threads == 0 && !find(team)) {
+    // a shape compiled for fewer team sizes (LQ with nx = 16: 32 threads) takes the one it has
+    for (int alt : {32, 64, 128, 256})
+      if (find(alt)) { team = alt; break; }
+  }
   const int ws = make_layout(nx, nu, K, team, o.exact_hessian, implicit).total_floats;
   const size_t ws_bytes = (size_t)ws * sizeof(float);
   const bool use_gws = ws_bytes > (size_t)smem_optin;
@@ -149,16 +163,7 @@ extern "C" dmpc_err dmpc_solve_noalloc(const dmpc_ocp_desc* desc, int batch, con
     grid = (int)std::min<size_t>({(size_t)grid, (size_t)2 * n_sm, fit});
   }
 
-  LaunchFn fn = nullptr;
-  {
-    KernelEntry table[kMaxKernelEntries];
-    const int n = collect_kernel_entries(table);
-    for (int i = 0; i < n; ++i)
-      if (table[i].team == team && table[i].model == kmodel && table[i].nx == nx && table[i].nu == nu) {
-        fn = table[i].fn;
-        break;
-      }
-  }
+  LaunchFn fn = find(team);
   if (!fn) return DMPC_E_UNSUPPORTED;
 
   void* base = nullptr;
@@ -190,6 +195,7 @@ extern "C" dmpc_err dmpc_solve_noalloc(const dmpc_ocp_desc* desc, int batch, con
   P.opt.ru_delta = o.ru_delta;
   P.opt.pcg_precision = o.pcg_precision;
   P.opt.exact_hessian = o.exact_hessian;
+  P.opt.pcg_variant = o.pcg_variant;
   P.x_s = x_s; P.theta = theta; P.x_ref = x_ref;
   P.z_init = z_init; P.lam_init_f = lam_init;
   P.z_out = z_out; P.lam_out = lam_out;

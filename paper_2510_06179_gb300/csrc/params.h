@@ -26,6 +26,7 @@ struct Options {
   float ru_delta;       // reliable-update trigger: eta drops by ru_delta^2
   int pcg_precision;    // 0: FP32 iteration + FP64 reliable updates; 1: double-float throughout
   int exact_hessian;    // backward KKT matrix: 0 Gauss-Newton, 1 exact Hessian of the Lagrangian
+  int pcg_variant;      // 0: Algorithm 4 as printed; 1: one-reduction reorganisation (single-warp teams)
 };
 
 enum KernelMode : int { MODE_SOLVE = 0, MODE_INSPECT = 1, MODE_VJP = 2 };

@@ -1,9 +1,12 @@
 // The plain one-launch-per-step form of the same method: every step of an SQP iteration
 // (load, linearise, Schur blocks, preconditioner, each PCG operation of Algorithm 4, recovery,
 // line search, outputs) is its own kernel launch over the batch, the per-OCP workspace (the S
-// and Phi^-1 blocks included) lives in HBM, the PCG scalars of each OCP are kept in HBM between
-// launches, and the host polls convergence.  It reuses the stage functions of the fused form,
-// so both compute the same arithmetic; it is the comparator the fused form is measured against.
+// and Phi^-1 blocks included) lives in HBM and the PCG scalars of each OCP are kept in HBM
+// between launches.  The launches of a solve form one CUDA graph; each PCG solve is a
+// conditional WHILE node whose body (a few PCG iterations, then plain_pcg_continue) repeats
+// until no OCP of the batch is still iterating, so convergence is decided on the device with no
+// host round trip.  It reuses the stage functions of the fused form, so both compute the same
+// arithmetic; it is the comparator the fused form is measured against.
 #pragma once
 #include "fused.cuh"
 
@@ -245,10 +248,12 @@ __device__ void plain_one(const KParams& P, PlainState* st, int ocp, int step, i
   if (c.tm.lane == 0) S.status = c.status;
 }
 
-// One block = one team = one OCP; one launch = one step for the whole batch.
+// One block = one team = one OCP; one launch = one step for the whole batch.  The parameters
+// live in device memory (written once per solve), so one captured graph serves every solve.
 template <int TEAM, class... Ms>
-__global__ void __launch_bounds__(256, 1) plain_kernel(const __grid_constant__ KParams P, PlainState* st, int step,
+__global__ void __launch_bounds__(256, 1) plain_kernel(const KParams* __restrict__ Pp, PlainState* st, int step,
                                                         int s_iter) {
+  const KParams& P = *Pp;
   if ((int)blockIdx.x >= P.n_work) return;
   const int ocp = P.order ? P.order[blockIdx.x] : (int)blockIdx.x;
   const OcpRec& o = P.ocps[ocp];
@@ -258,7 +263,8 @@ __global__ void __launch_bounds__(256, 1) plain_kernel(const __grid_constant__ K
   (void)done;
 }
 
-// Number of OCPs whose PCG is still iterating (the host polls it).
-__global__ void plain_count_active(const PlainState* st, const int* order, int n, int* out);
+// Last node of a PCG WHILE body: keeps the loop running while any OCP of the work list is
+// still iterating (every OCP stops within pcg_max_iters iterations, so the loop ends).
+__global__ void plain_pcg_continue(const PlainState* st, const KParams* P, cudaGraphConditionalHandle cond);
 
 }  // namespace dmpc

@@ -29,10 +29,12 @@ int collect_kernel_entries(KernelEntry* out) {
   n += DMPC_REGISTER_NAME(model, 128)(out + n);      \
   n += DMPC_REGISTER_NAME(model, 256)(out + n);
   DMPC_COLLECT(lq)
+  DMPC_COLLECT(lq16)
   DMPC_COLLECT(pendulum)
   DMPC_COLLECT(cartpole)
   DMPC_COLLECT(bicycle)
   DMPC_COLLECT(single_track)
+  DMPC_COLLECT(single_track_rate)
   DMPC_COLLECT(rigid_body)
   DMPC_COLLECT(attitude)
   DMPC_COLLECT(mixed)

@@ -21,6 +21,7 @@ MODELS = {
     "single_track": dict(id=4, nx=6, nu=2, p_shared=2, integrator="rk4"),
     "rigid_body12": dict(id=5, nx=12, nu=4, p_shared=4, integrator="rk4"),
     "attitude":     dict(id=6, nx=3, nu=3, p_shared=3, integrator="euler"),
+    "single_track_rate": dict(id=7, nx=8, nu=2, p_shared=2, integrator="rk4"),
 }
 MODEL_NAMES = {v["id"]: k for k, v in MODELS.items()}
 
@@ -297,6 +298,27 @@ def vehicle_config(B=1024, T=100, seed=0, sqp_iters=10, pcg_tol=1e-6, dt=0.02, w
     return Workload("vehicle", "single_track", 6, 2, T, dt, _f32(x_s), _f32(th), _f32(ref),
                     sqp_iters=sqp_iters, line_search=True, pcg_tol=pcg_tol,
                     u_target=_f32(np.zeros((B, 2))), extra=dict(features=_f32(feats)))
+
+
+def vehicle_rate_config(B=64, T=50, seed=0, sqp_iters=10, pcg_tol=1e-6, dt=0.02):
+    """The single-track vehicle with control-rate augmentation (App. B.3): state (px, py, psi, r,
+    Vy, Vx, delta, Fx), input (delta rate, Fx rate).  Inputs as in vehicle_config; the initial
+    steer and drive force are 0 and the reference holds them at 0.  Weights: state as the
+    vehicle's tracking tune, the inputs themselves U-log around (1, 1e-6), their rates around
+    (0.1, 1e-8) (the drive force changes by thousands of newtons per second)."""
+    base = vehicle_config(B=B, T=T, seed=seed, sqp_iters=sqp_iters, pcg_tol=pcg_tol, dt=dt)
+    rng = np.random.default_rng(seed + 7919)
+    x_s = np.concatenate([base.x_s, np.zeros((B, 2))], 1)
+    x_ref = np.concatenate([base.x_ref, np.zeros((B, T + 1, 2))], 2)
+    lay = theta_layout("single_track", 6, 2, T)
+    q_x = base.theta[:, lay["q"]:lay["q"] + 6].astype(np.float64)
+    q_u = np.array([1.0, 1e-6]) * np.exp(rng.uniform(-1, 1, size=(B, 2)))
+    r = np.array([0.1, 1e-8]) * np.exp(rng.uniform(-1, 1, size=(B, 2)))
+    q = np.concatenate([q_x, q_u], 1)
+    th = _pack_theta("single_track_rate", 8, 2, T, base.theta[:, :2].astype(np.float64), None, q, r, 10.0 * q)
+    return Workload("vehicle_rate", "single_track_rate", 8, 2, T, dt, _f32(x_s), _f32(th), _f32(x_ref),
+                    sqp_iters=sqp_iters, line_search=True, pcg_tol=pcg_tol,
+                    u_target=_f32(np.zeros((B, 2))), extra=dict(features=base.extra["features"]))
 
 
 def rigid_body_config(B=16, T=64, seed=0, sqp_iters=5, pcg_tol=1e-6, dt=0.02):

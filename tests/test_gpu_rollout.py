@@ -33,11 +33,13 @@ def _oracle_reward(prob, q):
     return R
 
 
-def test_rollout_gradient_matches_oracle_finite_differences():
+@pytest.mark.parametrize("problem", [2, 5])
+def test_rollout_gradient_matches_oracle_finite_differences(problem):
+    """Problem 2 (nx 8, nu 4) and problem 5 (nx 16, nu 8) of the RL table, shortened."""
     import torch
     from paper_2510_06179_gb300.rollout import make_batch, closed_loop_reward
     ensure_built()
-    prob = workloads.rl_lq_problem(2, seed=3, B=3, H=4, T=12)
+    prob = workloads.rl_lq_problem(problem, seed=3, B=3, H=4, T=12)
     prob.x0 = (prob.x0 / 5.0).astype(np.float32)     # keep the closed loop well scaled
     batch = make_batch(prob, "cuda:0")
     q = torch.from_numpy(prob.q0.copy()).to("cuda:0").requires_grad_(True)

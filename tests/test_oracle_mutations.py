@@ -17,6 +17,7 @@ from tests import test_oracle_cost as COST
 from tests import test_oracle_implicit as IMPL
 from tests import test_oracle_kkt as KKT
 from tests import test_oracle_models as MODELS
+from tests import test_oracle_rate as RATE
 from tests import test_oracle_sqp as SQP
 from tests import test_oracle_vjp as VJP
 
@@ -361,6 +362,14 @@ def _dF_dtheta_fiala_columns_swapped(mp):
     _patch_all(mp, BW, "dF_dtheta", mutant)
 
 
+def _control_rate_without_dt(mp):
+    def mutant(self, x, u, ths, thk):
+        nb = self.base.nx
+        xb, ub = list(x[:nb]), list(x[nb:])
+        return list(self.base.step(xb, ub, ths, thk)) + [ub[i] + u[i] for i in range(self.nu)]   # planted: no dt
+    mp.setattr(MD.ControlRate, "step", mutant)
+
+
 def _implicit_a_plus_transposed(mp):
     orig = O.linearise
 
@@ -431,6 +440,8 @@ CASES = {
         _dF_dtheta_cost_rows_without_reference, lambda: VJP.test_dF_dtheta_matches_differenced_residual("kin_bicycle")),
     "dF/dtheta friction and cornering-stiffness columns swapped (vehicle, Eq. 3)": (
         _dF_dtheta_fiala_columns_swapped, lambda: VJP.test_dF_dtheta_matches_differenced_residual("single_track")),
+    "control-rate augmentation integrating the rate without dt (App. B.3)": (
+        _control_rate_without_dt, RATE.test_augmented_step_reproduces_the_base_trajectory),
     "implicit integrator's A^+ transposed (Eq. 4)": (
         _implicit_a_plus_transposed,
         lambda: IMPL.test_implicit_linearisation_matches_differences(IMPL.workloads.cartpole_config)),
