@@ -27,7 +27,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "OCP solve+grad/s at ≤1e-4 rel err vs FP64; serving p50/p99 ms vs plain form"
 UNIT = "OCP solve+grad/s"
-B, T, SQP_ITERS, PCG_TOL = 256, 50, 10, 5e-8
+B, T, SQP_ITERS, PCG_TOL = 256, 50, 10, 1e-7
 WORKLOAD = "cartpole B=256 nx=4 nu=1 T=50 dt=0.05 RK4, 10 SQP iters + line search, fwd+bwd"
 L2_FLUSH_BYTES = 256 << 20
 
@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=256, help="OCPs in the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement of the JSON line")
+    ap.add_argument("--profile-case", choices=["cartpole", "vehicle"], default=None,
+                    help="run a small untimed case for a profiler and exit: the bench batch (three warm-up "
+                         "forward launches, then one forward and one backward launch), or a one-wave vehicle "
+                         "batch (152 OCPs, T 100; three warm-up forward launches, then one)")
     ap.add_argument("--suite", default=None, help="also run the comparison suite and write it to this JSON file")
     ap.add_argument("--suite-only", action="store_true", help="run only the comparison suite")
     return ap.parse_args()
@@ -85,7 +89,7 @@ def throughput(world, steps, seconds):
 # bench step (the command and counters are summarised under profiles/), with the hash of the
 # kernel sources it was taken on; reported only while the sources still hash the same.  The hash
 # ignores comments and whitespace, so only an edit of the code itself invalidates a capture.
-TRAFFIC_CAPTURE = {"src_sha256_16": "c82ffdbbaa856498", "bytes_per_launch": 625664 + 150528}
+TRAFFIC_CAPTURE = {"src_sha256_16": "0c6615f18db33776", "bytes_per_launch": 631296 + 141824}
 
 
 def _code_tokens(text):
@@ -273,6 +277,35 @@ def algorithmic_flops(pcg_iters_fwd, pcg_iters_bwd, nx=4, nu=1):
     return fwd, bwd
 
 
+def profile_case(name):
+    """Launches of one small case with no timing, for a profiler to capture (`--profile-case`)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2510_06179_gb300 import workloads
+    from paper_2510_06179_gb300.solver import OCPBatch
+    dev = torch.device("cuda", 0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32).reshape(-1)).to(dev)
+    if name == "cartpole":
+        w = workload(0)
+        b = OCPBatch(("cartpole", 4, 1, T, 0.05), batch=B, device=dev, sqp_iters=SQP_ITERS, line_search=1,
+                     pcg_tol=PCG_TOL, warm_start=0)
+    else:
+        w = workloads.vehicle_config(B=152, T=100, seed=0, sqp_iters=SQP_ITERS)
+        b = OCPBatch(("single_track", 6, 2, 100, 0.02), batch=152, device=dev, sqp_iters=SQP_ITERS, line_search=1,
+                     pcg_tol=PCG_TOL, warm_start=0)
+    inp = (t(w.x_s), t(w.theta), t(w.x_ref))
+    for _ in range(4):
+        b.solve(*inp, want_stats=False)
+    if name == "cartpole":
+        dl = torch.zeros(w.B * w.n, device=dev)
+        dl.view(w.B, -1)[:, 4] = 1.0
+        b.vjp(dl, want_stats=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": name, "tiling": b.get_tiling()}))
+    b.close()
+
+
 def measured_probes():
     """(FP32 FMA peak in TFLOP/s, microseconds per FP32 PCG iteration of one warp alone) from the
     library's probes, or (None, None) if a probe fails."""
@@ -332,6 +365,8 @@ def main():
         return reference_arm(args, rank, world)
     if args.suite_only:
         return suite(args.suite or "suite.json")
+    if args.profile_case:
+        return profile_case(args.profile_case)
     import torch
     import torch.distributed as dist
     if world > 1:

@@ -107,6 +107,15 @@ def test_cartpole_forward_parity():
     b.close()
 
 
+def test_cartpole_one_reduction_pcg_parity():
+    """pcg_variant = 1 (Algorithm 4 reorganised with one fused reduction per iteration) meets the
+    same solution and gradient gates under the replay protocol."""
+    w = workloads.cartpole_config(B=64, T=50, seed=0)
+    b, g, ref = _nonlinear_forward(w, pcg_variant=1, pcg_tol=5e-8)
+    _grad_check(w, b, g)
+    b.close()
+
+
 def test_cartpole_double_float_pcg_parity():
     """pcg_precision = 1: the whole PCG solve in double-float arithmetic (single-warp teams)
     meets the same solution and gradient gates, and no OCP needs the rescue."""
