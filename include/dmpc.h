@@ -71,8 +71,9 @@ typedef enum {
 #define DMPC_S_CHOL_FAIL 32      /* a diagonal Schur block failed Cholesky (diagonal fallback used) */
 #define DMPC_S_FP64_RESCUE 64    /* informational: a PCG solve whose FP32 iteration stagnated or broke
                                     down was finished in extended precision (FP64 or double-float) */
-#define DMPC_S_HESS_INDEF 128    /* exact-Hessian vjp: a per-knot block of the Lagrangian Hessian was not
-                                    positive definite; its Gauss-Newton block was used instead */
+#define DMPC_S_HESS_INDEF 128    /* exact-Hessian vjp: the exact reduced Hessian was not positive definite
+                                    at some knot (a Riccati pivot block failed Cholesky), so this OCP's
+                                    gradient is the Gauss-Newton one instead */
 
 typedef enum {
   DMPC_MODEL_LQ = 0,
@@ -124,8 +125,10 @@ typedef struct {
                           others behave as 0); default 0 */
   int exact_hessian;   /* 1: dmpc_vjp uses the exact Hessian of the Lagrangian in the KKT matrix (the
                           dynamics curvature weighted by the forward multipliers, Sec. 3.4), so the
-                          gradient is exact for nonlinear dynamics; 0: Gauss-Newton (the paper's
-                          default); enlarges the workspace by (nx+nu)^2 doubles per knot; default 0 */
+                          gradient is exact for nonlinear dynamics (an OCP whose exact reduced Hessian
+                          is not positive definite gets the Gauss-Newton gradient and status bit
+                          DMPC_S_HESS_INDEF); 0: Gauss-Newton (the paper's default); enlarges the
+                          workspace by (nx+nu)^2 doubles per knot; default 0 */
   int pcg_variant;     /* 0: Algorithm 4 as printed (two dependent reductions per iteration); 1: the same
                           iteration reorganised after Chronopoulos and Gear (one fused reduction of r^T u
                           and (S u)^T u per iteration, S p by recurrence; equal in exact arithmetic);
@@ -210,7 +213,8 @@ long long dmpc_device_bytes(const dmpc_handle* h);
  * and write a record per OCP at record + rec_off[b] (rec_off from dmpc_inspect_offsets):
  *   A_t (T nx nx), B_t (T nx nu), C_t (T nx), g (K nx: x_0 - x_s, f_0..f_{T-1}),
  *   D, O, Pd, Po (K nx nx each; S_spd and Phi^-1 block rows, O_k couples k to k-1),
- *   gamma_spd (K nx), lambda+ (K nx), z+ (n), PCG iterations (1).  lam may be NULL (0). */
+ *   gamma_spd (K nx), lambda+ (K nx), z+ (n), PCG iterations (1), of them in the extended-
+ *   precision rescue (1).  lam may be NULL (0). */
 dmpc_err dmpc_qp_inspect(dmpc_handle* h, const float* x_s, const float* theta, const float* x_ref,
                          const float* z, const float* lam, float* record);
 dmpc_err dmpc_inspect_offsets(const dmpc_handle* h, long long* rec_off /* batch+1 */);

@@ -220,11 +220,11 @@ static dmpc_err configure_tiling(dmpc_handle* h, int team, int tpb) {
   if (team == 0) {
     // one knot per lane (register-resident PCG) when it fits, else a few knots per lane:
     // nx <= 4: one warp with one or two knots per lane up to K = 64; nx <= 6: one knot per lane
-    // (64 to 256 threads); larger nx: shared-memory PCG with 32 / 64 / 128 threads by K
+    // (64 to 256 threads); larger nx: shared-memory PCG with one knot per thread up to 256
     if (maxnx <= 6 && maxK <= 256)
       team = maxK <= 64 ? (maxnx <= 4 ? 32 : 64) : (maxK <= 128 ? 128 : 256);
-    else
-      team = maxK <= 32 ? 32 : (maxK <= 64 ? 64 : (maxK <= 320 ? 128 : 256));
+    else  // one knot per thread up to 256 threads (12-state rigid body, T 241: 107 ms on 256 against 195 on 128)
+      team = maxK <= 32 ? 32 : (maxK <= 64 ? 64 : (maxK <= 128 ? 128 : 256));
   }
   if (h->uniform && team_is_default) {
     // a shape compiled for fewer team sizes (LQ with nx = 16: 32 threads) takes the one it has
@@ -349,7 +349,7 @@ extern "C" dmpc_err dmpc_create_problem_batch(const dmpc_ocp_desc* descs, int ba
     h->tot_store += (long long)K * (5 * d.nx * d.nx + d.nx * d.nu);
     h->rec_off[b] = h->tot_rec;
     h->tot_rec += (long long)d.T * (d.nx * d.nx + d.nx * d.nu + d.nx) + (long long)K * d.nx +
-                  4LL * K * d.nx * d.nx + 2LL * K * d.nx + r.n + 1;
+                  4LL * K * d.nx * d.nx + 2LL * K * d.nx + r.n + 2;
     cost[b] = (double)K * d.nx * d.nx * (d.nx + 4);
   }
   h->rec_off[batch] = h->tot_rec;

@@ -106,6 +106,7 @@ struct Ctx {
   double* db;
   float* fb;
   int status;
+  int df_iters;  // PCG iterations of the current solve run in the double-float rescue (inspect output)
   bool exact;  // backward with the exact Hessian of the Lagrangian (Riccati solve), else Gauss-Newton
 
   __device__ __forceinline__ float* F(int off) const { return fb + off; }
@@ -1301,7 +1302,9 @@ __device__ __noinline__ int stage_pcg(Ctx<M, TEAM>& c) {
   if (!converged) {
     // per-OCP double-float rescue of this solve, continuing from the folded solution
     c.status |= ST_FP64_RESCUE;
-    it += stage_pcg_df<M, TEAM>(c, eta0, maxit);
+    const int d = stage_pcg_df<M, TEAM>(c, eta0, maxit);
+    c.df_iters += d;
+    it += d;
   }
   return it;
 }
@@ -1500,7 +1503,9 @@ __device__ __noinline__ int stage_pcg_reg(Ctx<M, TEAM>& c) {
   c.tm.buf = tm.buf;
   if (!converged) {
     c.status |= ST_FP64_RESCUE;
-    it += stage_pcg_df<M, TEAM>(c, eta0, maxit);
+    const int d = stage_pcg_df<M, TEAM>(c, eta0, maxit);
+    c.df_iters += d;
+    it += d;
   }
   return it;
 }
@@ -1852,7 +1857,11 @@ __device__ __noinline__ int stage_pcg_warp(Ctx<M, 32>& c) {
     for (int i = 0; i < NX; ++i) e0[0] = fmaf(r[j][i], z[j][i], e0[0]);
   warp_sum(e0);
   const float eta0 = e0[0];
-  if (P.opt.pcg_precision == 1) return stage_pcg_warp_df<M, KPL>(c, eta0, P.opt.pcg_max_iters);
+  if (P.opt.pcg_precision == 1) {
+    const int d = stage_pcg_warp_df<M, KPL>(c, eta0, P.opt.pcg_max_iters);
+    c.df_iters += d;
+    return d;
+  }
   // true residual of the initial guess, preconditioned residual, first direction
   hp_residual<M, 32>(c, LP);
 #pragma unroll
@@ -1945,7 +1954,9 @@ __device__ __noinline__ int stage_pcg_warp(Ctx<M, 32>& c) {
   }
   if (!converged) {
     c.status |= ST_FP64_RESCUE;
-    it += stage_pcg_warp_df<M, KPL>(c, eta0, maxit);
+    const int d = stage_pcg_warp_df<M, KPL>(c, eta0, maxit);
+    c.df_iters += d;
+    it += d;
   }
   return it;
 }
@@ -1999,7 +2010,11 @@ __device__ __noinline__ int stage_pcg_warp_cg(Ctx<M, 32>& c) {
     for (int i = 0; i < NX; ++i) e0[0] = fmaf(r[j][i], u[j][i], e0[0]);
   warp_sum(e0);
   const float eta0 = e0[0];
-  if (P.opt.pcg_precision == 1) return stage_pcg_warp_df<M, KPL>(c, eta0, P.opt.pcg_max_iters);
+  if (P.opt.pcg_precision == 1) {
+    const int d = stage_pcg_warp_df<M, KPL>(c, eta0, P.opt.pcg_max_iters);
+    c.df_iters += d;
+    return d;
+  }
   // true residual of the initial guess; u = Phi^-1 r, w = S u, gamma = r^T u, delta = w^T u
   hp_residual<M, 32>(c, LP);
 #pragma unroll
@@ -2111,7 +2126,9 @@ __device__ __noinline__ int stage_pcg_warp_cg(Ctx<M, 32>& c) {
   }
   if (!converged) {
     c.status |= ST_FP64_RESCUE;
-    it += stage_pcg_warp_df<M, KPL>(c, eta0, maxit);
+    const int d = stage_pcg_warp_df<M, KPL>(c, eta0, maxit);
+    c.df_iters += d;
+    it += d;
   }
   return it;
 }
@@ -2340,7 +2357,8 @@ __device__ __noinline__ void write_inspect(Ctx<M, TEAM>& c, int iters) {
   const int T = c.T, K = c.K, KP = c.KP;
   float* out = c.P->inspect + c.P->inspect_off[c.ocp];
   // record: A (T nx nx), B (T nx nu), C (T nx), f (K nx), D, O, Pd, Po (K nx nx each),
-  // gamma (K nx), lambda+ (K nx), z+ (n), pcg iterations (1); knot-major, row-major blocks
+  // gamma (K nx), lambda+ (K nx), z+ (n), pcg iterations (1), of them in the double-float
+  // rescue (1); knot-major, row-major blocks
   long long o = 0;
   for (int k = c.tm.lane; k < K; k += TEAM) {
     if (k >= 1) {
@@ -2367,7 +2385,10 @@ __device__ __noinline__ void write_inspect(Ctx<M, TEAM>& c, int iters) {
     for (int e = 0; e < NX; ++e) out[oz + (long long)k * NZ + e] = c.F(c.L.xp)[e * KP + k];
     if (k < T)
       for (int e = 0; e < NU; ++e) out[oz + (long long)k * NZ + NX + e] = c.F(c.L.up)[e * KP + k];
-    if (k == 0) out[oz + (long long)K * NX + (long long)T * NU] = (float)iters;
+    if (k == 0) {
+      out[oz + (long long)K * NX + (long long)T * NU] = (float)iters;
+      out[oz + (long long)K * NX + (long long)T * NU + 1] = (float)c.df_iters;
+    }
   }
 }
 
@@ -2646,7 +2667,19 @@ __device__ __noinline__ void run_backward(Ctx<M, TEAM>& c) {
     stage_linearise<M, TEAM>(c);
     stage_exact_hessian<M, TEAM>(c);
     stage_riccati_exact<M, TEAM>(c);
-    stage_bwd_finish<M, TEAM>(c, 0);
+    if (!(c.status & ST_HESS_INDEF)) {
+      stage_bwd_finish<M, TEAM>(c, 0);
+      return;
+    }
+    // the exact reduced Hessian is not positive definite at some knot (the point is not a strict
+    // local minimum in the exact second-order sense): this OCP gets the Gauss-Newton gradient,
+    // flagged, from the linearisation already in the workspace
+    c.exact = false;
+    stage_schur<M, TEAM>(c, false);
+    stage_precond<M, TEAM>(c);
+    stage_bwd_rhs<M, TEAM>(c);
+    const int it = run_pcg<M, TEAM>(c);
+    stage_bwd_finish<M, TEAM>(c, it);
     return;
   }
   if (P.store_mode && P.store && !is_implicit<M>::value) {  // stored records carry no A^+
@@ -2675,6 +2708,7 @@ __device__ void run_one(const KParams& P, int ocp, float* ws, int lane, int team
   c.db = reinterpret_cast<double*>(ws);
   c.fb = ws;
   c.status = 0;
+  c.df_iters = 0;
   c.exact = !is_lq<M>::value && !is_implicit<M>::value && P.opt.exact_hessian && P.mode == MODE_VJP;
   c.tm.lane = lane;
   c.tm.bar_id = team_in_block + 1;

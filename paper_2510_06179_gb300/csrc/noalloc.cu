@@ -127,7 +127,7 @@ extern "C" dmpc_err dmpc_solve_noalloc(const dmpc_ocp_desc* desc, int batch, con
   int team = o.team_threads;
   if (team == 0) {
     if (nx <= 6 && K <= 256) team = K <= 64 ? (nx <= 4 ? 32 : 64) : (K <= 128 ? 128 : 256);
-    else team = K <= 32 ? 32 : (K <= 64 ? 64 : (K <= 320 ? 128 : 256));
+    else team = K <= 32 ? 32 : (K <= 64 ? 64 : (K <= 128 ? 128 : 256));
   }
   if (team != 32 && team != 64 && team != 128 && team != 256) return DMPC_E_ARG;
   KernelEntry table[kMaxKernelEntries];

@@ -84,8 +84,14 @@ __device__ __noinline__ void plain_step(Ctx<M, TEAM>& c, PlainState& S, int step
       if (c.exact) stage_exact_hessian<M, TEAM>(c);
       break;
     case PS_SCHUR:  // exact-Hessian backward: the Riccati solve replaces a2-a4
-      if (c.exact) stage_riccati_exact<M, TEAM>(c);
-      else stage_schur<M, TEAM>(c, P.mode != MODE_VJP);
+      if (c.exact) {
+        stage_riccati_exact<M, TEAM>(c);
+        // reduced Hessian not positive definite: the Gauss-Newton gradient instead (the later
+        // steps see the flag and take the Gauss-Newton path)
+        if (c.status & ST_HESS_INDEF) stage_schur<M, TEAM>(c, false);
+      } else {
+        stage_schur<M, TEAM>(c, P.mode != MODE_VJP);
+      }
       break;
     case PS_PREC:
       if (!c.exact) stage_precond<M, TEAM>(c);
@@ -243,6 +249,8 @@ __device__ void plain_one(const KParams& P, PlainState* st, int ocp, int step, i
   c.tm.buf = 0;
   PlainState& S = st[ocp];
   c.status = S.status;
+  c.df_iters = 0;
+  if (step != PS_LOAD && (S.status & ST_HESS_INDEF)) c.exact = false;   // Gauss-Newton fallback
   plain_step<M, TEAM>(c, S, step, s_iter);
   c.status = c.tm.bor(c.status);
   if (c.tm.lane == 0) S.status = c.status;

@@ -171,7 +171,8 @@ class OCPBatch:
         out, o = {}, 0
         for name, shape in [("A", (T, nx, nx)), ("B", (T, nx, nu)), ("C", (T, nx)), ("g", (K, nx)),
                             ("D", (K, nx, nx)), ("O", (K, nx, nx)), ("Pd", (K, nx, nx)), ("Po", (K, nx, nx)),
-                            ("gamma", (K, nx)), ("lam", (K, nx)), ("z", (K * nx + T * nu,)), ("iters", (1,))]:
+                            ("gamma", (K, nx)), ("lam", (K, nx)), ("z", (K * nx + T * nu,)), ("iters", (1,)),
+                            ("rescue_iters", (1,))]:
             size = int(np.prod(shape))
             out[name] = r[o:o + size].reshape(shape)
             o += size

@@ -2,7 +2,9 @@
 full Hessian of the Lagrangian, dynamics curvature weighted by the forward multipliers
 (Sec. 3.4 contrasts it with the Gauss-Newton matrix).  Checked against the oracle's exact-
 Hessian VJP at the GPU's own (z, lambda); the oracle's version is itself pinned against
-finite differences of the converged solution."""
+finite differences of the converged solution.  An OCP whose exact reduced Hessian is not
+positive definite (status bit 128) returns the Gauss-Newton gradient and is checked against the
+oracle's Gauss-Newton VJP, so every OCP is gated."""
 import numpy as np
 import pytest
 
@@ -17,27 +19,29 @@ G_GATE = 1e-3
 HESS_INDEF = 128
 
 
-def _exact_vs_oracle(w, min_checked, **opt):
+def _exact_vs_oracle(w, min_exact, **opt):
     b, g = gpu_solve(w, exact_hessian=1, **opt)
     dl = w.dl_dz(g["z"])
     gv = gpu_vjp(b, w, dl)
     ref = oracle_vjp(to_ocp(w), g["z"], g["lam"], dl, hessian="exact")
     gn = oracle_vjp(to_ocp(w), g["z"], g["lam"], dl, hessian="gn")
     ok = (gv["status"] & HESS_INDEF) == 0
-    e = rel_err(gv["dtheta"], ref["dtheta"])
-    ex = rel_err(gv["dxs"], ref["dxs"])
+    want_th = np.where(ok[:, None], ref["dtheta"], gn["dtheta"])
+    want_xs = np.where(ok[:, None], ref["dxs"], gn["dxs"])
+    e = rel_err(gv["dtheta"], want_th)
+    ex = rel_err(gv["dxs"], want_xs)
     gap = rel_err(gn["dtheta"], ref["dtheta"])
-    print(f"exact[{w.name}] checked {ok.sum()}/{w.B} dtheta_err_max {e[ok].max():.2e} "
-          f"dxs_err_max {ex[ok].max():.2e} GN-vs-exact gap median {np.median(gap):.2e}")
-    assert ok.sum() >= min_checked
-    assert e[ok].max() <= G_GATE and ex[ok].max() <= G_GATE
+    print(f"exact[{w.name}] exact {ok.sum()}/{w.B}, Gauss-Newton fallback {(~ok).sum()}; dtheta_err_max "
+          f"{e.max():.2e} dxs_err_max {ex.max():.2e} GN-vs-exact gap median {np.median(gap):.2e}")
+    assert ok.sum() >= min_exact
+    assert e.max() <= G_GATE and ex.max() <= G_GATE
     b.close()
     return gv, gap
 
 
 def test_cartpole_exact_hessian_gradient():
     w = workloads.cartpole_config(B=32, T=40, seed=5)
-    gv, gap = _exact_vs_oracle(w, min_checked=24)
+    gv, gap = _exact_vs_oracle(w, min_exact=24)
     # on nonlinear dynamics the two matrices give different gradients
     assert np.median(gap) > 1e-6
 
@@ -46,13 +50,13 @@ def test_cartpole_exact_hessian_gradient():
 def test_other_models_exact_hessian_gradient(name):
     """(The single-track vehicle is left out: at its solutions the exact-Hessian KKT matrix has
     condition ~1e8 and a reduced Hessian with eigenvalues ~1e-6 against ~30, so the FP32
-    linearisation cannot determine that gradient; the oracle itself misses finite differences
-    there by 40 %.)"""
+    linearisation cannot determine that gradient; the oracle's exact-Hessian gradient on the
+    vehicle is pinned against finite differences on the CPU, tests/test_oracle_vjp.py.)"""
     w = {"pendulum": lambda: workloads.pendulum_config(B=16, T=25, seed=2),
          "attitude": lambda: workloads.attitude_config(),
          "bicycle": lambda: workloads.bicycle_config(B=16, T=30, seed=3, sqp_iters=6),
          "rigid_body": lambda: workloads.rigid_body_config(B=8, T=16, seed=2, sqp_iters=3)}[name]()
-    _exact_vs_oracle(w, min_checked=w.B // 2)
+    _exact_vs_oracle(w, min_exact=w.B // 2)
 
 
 def test_exact_hessian_equals_gauss_newton_on_affine_dynamics():
