@@ -1,9 +1,10 @@
 """Continuous-batching serving loop for OCP solves (the target's serving reshaping).
 
 Requests (one OCP each: model, horizon, x_s, theta, x_ref) arrive over time.  Shapes are
-grouped into classes (model x horizon bucket); each class owns a slot arena (one C-ABI handle
-whose OCPs are slots, sized by the device-memory budget) and a CUDA stream.  Every pass of the
-host loop, for each class whose previous tick has finished on the GPU:
+grouped into classes (model x horizon bucket); each class owns one or more slot arenas (a C-ABI
+handle whose OCPs are slots, with a CUDA stream), and takes another while its requests wait for a
+slot and the device-memory budget leaves room for one.  Every pass of the host loop, for each
+arena whose previous tick has finished on the GPU:
 
   1. retire: requests whose last SQP iteration ran in that tick are done (completion time =
      the tick's device event); their slots become free;
@@ -14,8 +15,8 @@ host loop, for each class whose previous tick has finished on the GPU:
      (dmpc_solve_subset, sqp_iters = 1); each slot continues from the iterate it left on the
      device, so a request admitted now runs alongside requests half-way through their solve.
 
-A class has at most one tick in flight, so requests that arrive while it runs wait at most one
-tick for admission instead of queueing behind launches the GPU has not reached; the classes'
+An arena has at most one tick in flight, so requests that arrive while it runs wait at most one
+tick for admission instead of queueing behind launches the GPU has not reached; the arenas'
 ticks overlap on their streams.  Latency = device completion time - host arrival time.
 `plain=True` runs the same loop on the plain one-launch-per-step form (dmpc_solve_subset_plain).
 """
@@ -53,7 +54,10 @@ class Request:
 
 
 class SlotClass:
-    def __init__(self, model, nx, nu, t_lo, t_hi, dt, slots, options, device, priority=0):
+    """One slot arena of a class: a C-ABI handle whose OCPs are slots, its input/output arrays
+    and stream.  A class may own several arenas; they share the class's queue."""
+
+    def __init__(self, model, nx, nu, t_lo, t_hi, dt, slots, options, device, priority=0, queue=None):
         self.model, self.nx, self.nu, self.t_hi = model, nx, nu, t_hi
         self.batch = OCPBatch((model, nx, nu, t_hi, dt), batch=slots, device=device, **options)
         self.stream = torch.cuda.Stream(device, priority=priority)
@@ -73,9 +77,13 @@ class SlotClass:
         self.slots = slots
         self.free = deque(range(slots))
         self.busy = {}              # slot -> [request, ticks launched]
-        self.queue = deque()
+        self.queue = queue if queue is not None else deque()
         self.inflight = None        # (event, [(slot, request) finishing in that tick])
         self.device = device
+
+    def tensor_bytes(self):
+        return sum(t.numel() * t.element_size() for t in (self.x_s, self.theta, self.x_ref, self.z, self.lam,
+                                                           self.status, self.idx_d))
 
     def idle(self):
         return self.inflight is None or self.inflight[0].query()
@@ -171,32 +179,67 @@ def class_priorities(shapes):
 
 
 class ServingEngine:
-    """Slot classes by (model, horizon bucket) under a device-memory budget."""
+    """Slot classes by (model, horizon bucket) under a device-memory budget.  Each class starts
+    with one arena of `slots_per_class` slots; while its requests wait for a slot and the budget
+    leaves room for another arena of the same size (its handle's device bytes, from
+    dmpc_device_bytes, plus its arrays), the class takes one more, up to `max_arenas_per_class`.
+    So admission is decided per request by slots and device memory: a request runs as soon as a
+    slot is free or can be paid for, and otherwise waits in its class's queue."""
 
     def __init__(self, shapes, budget_bytes, sqp_iters=5, slots_per_class=256, device="cuda:0", plain=False,
-                 **options):
+                 max_arenas_per_class=8, **options):
         """shapes: list of (model, nx, nu, dt) that requests may use."""
         self.device = torch.device(device)
         self.plain = plain
         self.sqp_iters = sqp_iters
+        self.budget = int(budget_bytes)
+        self.slots = slots_per_class
+        self.max_arenas = max_arenas_per_class
         opts = dict(sqp_iters=1, line_search=1, warm_start=1, pcg_tol=1e-7)
         opts.update(options)
-        self.classes = {}
-        used = 0
+        self.opts = opts
+        self.classes = {}           # key -> the class's first arena (shape, tiling)
+        self.arenas = {}            # key -> every arena of the class
+        self.queues = {}
+        self.spec = {}
+        self.bytes = 0
         prios = class_priorities(shapes)
         for model, nx, nu, dt in shapes:
             for lo, hi in T_BUCKETS:
-                c = SlotClass(model, nx, nu, lo, hi, dt, slots_per_class, opts, self.device, prios[(model, lo, hi)])
-                c.batch.sqp_iters_total = sqp_iters
-                used += int(self.lib_bytes(c))
-                self.classes[(model, lo, hi)] = c
-        if used > budget_bytes:
-            raise _lib.DMPCError(3, f"slot arenas need {used} bytes, budget {budget_bytes}")
-        self.bytes = used
+                key = (model, lo, hi)
+                self.spec[key] = (model, nx, nu, lo, hi, dt, prios[key])
+                self.queues[key] = deque()
+                c = self._new_arena(key)
+                self.classes[key] = c
+                self.arenas[key] = [c]
+                self.bytes += self.arena_bytes(c)
+        if self.bytes > self.budget:
+            raise _lib.DMPCError(3, f"slot arenas need {self.bytes} bytes, budget {self.budget}")
+
+    def _new_arena(self, key):
+        model, nx, nu, lo, hi, dt, prio = self.spec[key]
+        c = SlotClass(model, nx, nu, lo, hi, dt, self.slots, self.opts, self.device, prio, queue=self.queues[key])
+        c.batch.sqp_iters_total = self.sqp_iters
+        return c
 
     @staticmethod
     def lib_bytes(c):
         return c.lib.dmpc_device_bytes(c.batch.h)
+
+    def arena_bytes(self, c):
+        """Device memory of one arena: its handle (workspace, tables, resident state) and arrays."""
+        return int(self.lib_bytes(c)) + c.tensor_bytes()
+
+    def _grow(self, key):
+        """Another arena for class `key` if the budget and the arena cap allow, else None."""
+        arenas = self.arenas[key]
+        need = max(self.arena_bytes(a) for a in arenas)   # the plain form's workspace appears on first use
+        if len(arenas) >= self.max_arenas or self.bytes + need > self.budget:
+            return None
+        c = self._new_arena(key)
+        arenas.append(c)
+        self.bytes += self.arena_bytes(c)
+        return c
 
     def class_of(self, r):
         for (model, lo, hi), c in self.classes.items():
@@ -214,7 +257,6 @@ class ServingEngine:
         t0 = time.perf_counter()
         n_done = 0
         total = len(pending)
-        classes = list(self.classes.values())
         while n_done < total:
             now = time.perf_counter() - t0
             if now > max_seconds:
@@ -223,24 +265,32 @@ class ServingEngine:
                 r = pending.popleft()
                 self.class_of(r).queue.append(r)
             active = False
-            for c in classes:
-                if not c.idle():
-                    active = True
-                    continue
-                n_done += c.retire(start_ev, keep_solutions)
-                c.admit()
-                active = c.advance(self.plain, record_alpha=keep_solutions) or active
+            for key, arenas in self.arenas.items():
+                for c in arenas:
+                    if not c.idle():
+                        active = True
+                        continue
+                    n_done += c.retire(start_ev, keep_solutions)
+                    c.admit()
+                    active = c.advance(self.plain, record_alpha=keep_solutions) or active
+                if self.queues[key] and not any(c.free for c in arenas):
+                    c = self._grow(key)        # every slot taken and requests waiting
+                    if c is not None:
+                        c.admit()
+                        active = c.advance(self.plain, record_alpha=keep_solutions) or active
             if not active and pending:
                 time.sleep(max(0.0, min(1e-4, pending[0].arrival - (time.perf_counter() - t0))))
-        for c in classes:
-            if c.inflight is not None:
-                c.inflight[0].synchronize()
-                c.retire(start_ev, keep_solutions)
+        for arenas in self.arenas.values():
+            for c in arenas:
+                if c.inflight is not None:
+                    c.inflight[0].synchronize()
+                    c.retire(start_ev, keep_solutions)
         return requests
 
     def close(self):
-        for c in self.classes.values():
-            c.batch.close()
+        for arenas in self.arenas.values():
+            for c in arenas:
+                c.batch.close()
 
 
 def latency_stats(requests, warmup_fraction=0.1):

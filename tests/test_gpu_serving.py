@@ -91,3 +91,36 @@ def test_plain_form_serving_gives_the_same_results():
     print(f"plain vs fused serving: max rel diff {worst:.2e}")
     assert worst <= 1e-5
     e1.close(); e2.close()
+
+
+def test_arenas_grow_within_the_memory_budget():
+    """With two slots per arena, a burst makes classes take more arenas, never beyond the device-
+    memory budget or the arena cap; every request completes and matches the FP64 oracle (replay
+    protocol).  With a budget that leaves no room, nothing grows and requests wait for slots."""
+    import torch
+    from tests.oracle_helpers import replay_check
+    from paper_2510_06179_gb300.serving import ServingEngine, Request
+    ensure_built()
+    shapes = [s for s in workloads.SERVING_SHAPES if s[0] in ("pendulum", "cartpole")]
+    trace = workloads.serving_trace(rate=20000, duration=0.002, seed=21, T_lo=16, T_hi=40, shapes=shapes)
+    probe = ServingEngine(shapes, budget_bytes=16 << 30, sqp_iters=SQP, slots_per_class=2, pcg_tol=1e-9)
+    base = probe.bytes
+    probe.close()
+    for budget, may_grow in ((base + (256 << 20), True), (base, False)):
+        eng = ServingEngine(shapes, budget_bytes=budget, sqp_iters=SQP, slots_per_class=2, max_arenas_per_class=4,
+                            pcg_tol=1e-9)
+        reqs = [Request(rid=i, **d) for i, d in enumerate(trace)]
+        eng.run(reqs, keep_solutions=True, max_seconds=120)
+        torch.cuda.synchronize()
+        assert all(r.done is not None for r in reqs)
+        n_arenas = sum(len(a) for a in eng.arenas.values())
+        assert eng.bytes <= budget and all(len(a) <= 4 for a in eng.arenas.values())
+        assert (n_arenas > len(eng.arenas)) == may_grow, (n_arenas, len(eng.arenas))
+        for r in reqs[:6]:
+            w = workloads.Workload(f"req{r.rid}", r.model, r.nx, r.nu, r.T, r.dt, r.x_s[None], r.theta[None],
+                                   r.x_ref[None], sqp_iters=SQP, line_search=True)
+            res = replay_check(w, r.z[None].astype(np.float64), r.alpha[None])
+            assert res["consistent"][0] and res["ez"][0] <= 1e-4
+        print(f"budget {budget}: {len(reqs)} requests, {n_arenas} arenas over {len(eng.arenas)} classes, "
+              f"{eng.bytes} bytes")
+        eng.close()
