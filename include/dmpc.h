@@ -74,6 +74,8 @@ typedef enum {
 #define DMPC_S_HESS_INDEF 128    /* exact-Hessian vjp: the exact reduced Hessian was not positive definite
                                     at some knot (a Riccati pivot block failed Cholesky), so this OCP's
                                     gradient is the Gauss-Newton one instead */
+#define DMPC_S_SYNC_TIMEOUT 256  /* cluster form: a wait on another CTA of the OCP's thread-block cluster ran
+                                    out of time (4 s); the results of this OCP are not valid */
 
 typedef enum {
   DMPC_MODEL_LQ = 0,
@@ -133,6 +135,11 @@ typedef struct {
                           iteration reorganised after Chronopoulos and Gear (one fused reduction of r^T u
                           and (S u)^T u per iteration, S p by recurrence; equal in exact arithmetic);
                           single-warp teams (nx <= 4, K <= 64), the others behave as 0; default 0 */
+  int cluster_ctas;    /* OCPs whose workspace does not fit in one thread block's shared memory (12-state
+                          rigid body): 0 = run each on a thread-block cluster when one fits (its PCG
+                          solves distributed over the cluster's shared memory, CTAs per cluster chosen
+                          from the horizon), 1 = never (one team from global memory), 2..8 = clusters of
+                          that many CTAs; applies with team_threads = 0; default 0 */
 } dmpc_options;
 
 /* Fill *opt with the defaults above. */
@@ -270,13 +277,21 @@ dmpc_err dmpc_set_solution(dmpc_handle* h, const float* z, const float* lam, con
 /* Change the stream used by later calls. */
 dmpc_err dmpc_set_stream(dmpc_handle* h, void* cuda_stream);
 
-/* Override the tiling: threads per OCP (32/64/128/256) and OCPs per block (>= 1). */
+/* Override the tiling: threads per OCP (32/64/128/256) and OCPs per block (>= 1).  An explicit
+ * tiling runs every OCP on one team (no cluster form). */
 dmpc_err dmpc_set_tiling(dmpc_handle* h, int team_threads, int teams_per_block);
 
 /* Current tiling and per-team workspace: team threads, teams per block, grid size, dynamic
  * shared memory bytes per block (0 when the workspace is in global memory). */
 dmpc_err dmpc_get_tiling(const dmpc_handle* h, int* team_threads, int* teams_per_block, int* grid,
                          long long* smem_bytes);
+
+/* Cluster form of the handle (Algorithm 4 distributed over a thread-block cluster; see
+ * dmpc_options.cluster_ctas): CTAs per cluster, knots of the S and Phi^-1 blocks each CTA holds
+ * in shared memory, and clusters per launch; all 0 when the handle runs one team per OCP.
+ * Each pointer may be NULL.  In the cluster form CTA 0 of a cluster runs every other step of
+ * the OCP from its global workspace, and every CTA takes part in its PCG solves. */
+dmpc_err dmpc_get_cluster(const dmpc_handle* h, int* ctas_per_cluster, int* knots_per_cta, int* clusters);
 
 /* Release the handle and its device memory (synchronises its stream). NULL is ignored. */
 void dmpc_destroy(dmpc_handle* h);

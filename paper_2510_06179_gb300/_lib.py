@@ -23,7 +23,7 @@ class dmpc_options(ctypes.Structure):
                 ("ls_eta", c_float), ("feas_tol", c_float), ("pcg_tol", c_float), ("pcg_max_iters", c_int),
                 ("ru_delta", c_float), ("warm_start", c_int), ("store_schur", c_int),
                 ("team_threads", c_int), ("teams_per_block", c_int), ("pcg_precision", c_int),
-                ("exact_hessian", c_int), ("pcg_variant", c_int)]
+                ("exact_hessian", c_int), ("pcg_variant", c_int), ("cluster_ctas", c_int)]
 
 
 SIGNATURES = {
@@ -41,6 +41,7 @@ SIGNATURES = {
     "dmpc_solve_subset_plain": (c_int, [P, P, c_int, P, P, P, P, P, P, P, P]),
     "dmpc_device_bytes": (ctypes.c_longlong, [P]),
     "dmpc_inspect_offsets": (c_int, [P, P]),
+    "dmpc_get_cluster": (c_int, [P, P, P, P]),
     "dmpc_solve_noalloc": (c_int, [ctypes.POINTER(dmpc_ocp_desc), c_int, ctypes.POINTER(dmpc_options), P,
                                    P, P, P, P, P, P, P, P, P, P]),
     "dmpc_set_solution": (c_int, [P, P, P, P, P, P]),

@@ -72,6 +72,17 @@ std::mutex g_reg_mu;
 std::vector<KernelEntry> g_registry;
 std::string g_create_error;
 
+std::vector<ClusterEntry> g_cl_registry;
+std::once_flag g_cl_registry_once;
+const std::vector<ClusterEntry>& cluster_registry() {
+  std::call_once(g_cl_registry_once, [] {
+    ClusterEntry buf[kMaxClusterEntries];
+    const int n = collect_cluster_entries(buf);
+    g_cl_registry.assign(buf, buf + n);
+  });
+  return g_cl_registry;
+}
+
 const std::vector<KernelEntry>& registry() {
   std::lock_guard<std::mutex> lk(g_reg_mu);
   if (g_registry.empty()) {
@@ -123,6 +134,10 @@ struct dmpc_handle {
   size_t smem = 0;
   LaunchFn fn = nullptr;
   PlainFn plain_fn = nullptr;
+  // cluster form (distributed PCG): CTAs per cluster, knot capacity per CTA, clusters resident
+  bool use_cluster = false;
+  int cl_ncta = 0, cl_kc = 0, cl_max = 0;
+  ClusterLaunchFn cl_fn = nullptr;
   // plain one-launch-per-step form (allocated on first use)
   // serving: slot capacities (the shapes given at creation), cold-start flags, update staging
   std::vector<OcpRec> cap;
@@ -170,6 +185,7 @@ extern "C" void dmpc_default_options(dmpc_options* o) {
   o->pcg_precision = 0;
   o->exact_hessian = 0;
   o->pcg_variant = 0;
+  o->cluster_ctas = 0;
 }
 
 static Options to_kernel_options(const dmpc_options& o) {
@@ -207,6 +223,69 @@ static dmpc_err validate_options(dmpc_handle* h, const dmpc_options& o) {
   if (o.pcg_precision != 0 && o.pcg_precision != 1) return fail(h, DMPC_E_ARG, "pcg_precision must be 0 or 1");
   if (o.exact_hessian != 0 && o.exact_hessian != 1) return fail(h, DMPC_E_ARG, "exact_hessian must be 0 or 1");
   if (o.pcg_variant != 0 && o.pcg_variant != 1) return fail(h, DMPC_E_ARG, "pcg_variant must be 0 or 1");
+  if (o.cluster_ctas < 0 || o.cluster_ctas > kClMaxCtas)
+    return fail(h, DMPC_E_ARG, "cluster_ctas must be in [0, 8]");
+  return DMPC_OK;
+}
+
+static bool has_implicit_desc(const dmpc_handle* h) {
+  for (auto& d : h->descs)
+    if (is_implicit_desc(d)) return true;
+  return false;
+}
+
+// Cluster form for OCPs whose workspace does not fit in one CTA's shared memory: one cluster of
+// ncta CTAs per OCP, each holding ceil(K / ncta) knots of the PCG's blocks in shared memory.
+// cluster_ctas = 0 chooses ncta from the longest horizon (about 16 knots per CTA, at most 8 CTAs).
+// Leaves the single-team form in place when no cluster kernel fits.
+static dmpc_err configure_cluster(dmpc_handle* h, int maxK) {
+  const ClusterEntry* ce = nullptr;
+  for (auto& e : cluster_registry())
+    if (e.model == h->model0 && e.nx == h->nx0 && e.nu == h->nu0) ce = &e;
+  if (!ce) return DMPC_OK;
+  const int kc_max = cl_max_kc(h->nx0);
+  int ncta = h->opt.cluster_ctas;
+  if (ncta == 0) ncta = std::min(kClMaxCtas, std::max(2, (maxK + 15) / 16));
+  if (ncta < 2) return DMPC_OK;
+  const int kc = (maxK + ncta - 1) / ncta;
+  if (kc > kc_max) return DMPC_OK;
+  const size_t smem = (size_t)cl_layout(h->nx0, h->nu0, kc).total * sizeof(float);
+  if (smem > (size_t)h->smem_optin) return DMPC_OK;
+  const int fit = ce->max_clusters(ncta, smem);
+  if (fit < 1) return DMPC_OK;
+  // the leader runs the OCP as a 256-thread team: that team's kernels and workspace layout
+  LaunchFn fn = h->fn;
+  PlainFn pfn = h->plain_fn;
+  if (h->team != kClThreads) {
+    fn = nullptr;
+    for (auto& e : registry())
+      if (e.team == kClThreads && e.model == h->model0 && e.nx == h->nx0 && e.nu == h->nu0) { fn = e.fn; pfn = e.plain; }
+    if (!fn) return DMPC_OK;
+  }
+  int ws = 0;
+  for (auto& d : h->descs)
+    ws = std::max(ws, make_layout(d.nx, d.nu, d.T + 1, kClThreads, h->opt.exact_hessian, 0).total_floats);
+  const int ncl = std::min(h->batch, fit);
+  const size_t need = (size_t)ncl * ws;
+  if (need != h->gws_floats) {  // one slot per cluster (the single-team form may have sized it larger)
+    if (h->gws) cudaFree(h->gws);
+    h->gws = nullptr;
+    cudaError_t e = cudaMalloc(&h->gws, need * sizeof(float));
+    if (e != cudaSuccess) { h->gws_floats = 0; return fail(h, DMPC_E_OOM, "global workspace allocation failed"); }
+    h->gws_floats = need;
+  }
+  h->team = kClThreads;
+  h->fn = fn;
+  h->plain_fn = pfn;
+  h->max_ws_floats = ws;
+  h->use_cluster = true;
+  h->cl_ncta = ncta;
+  h->cl_kc = kc;
+  h->cl_max = ncl;
+  h->cl_fn = ce->fn;
+  h->tpb = 1;
+  h->grid = ncta * ncl;
+  h->smem = smem;
   return DMPC_OK;
 }
 
@@ -290,6 +369,11 @@ static dmpc_err configure_tiling(dmpc_handle* h, int team, int tpb) {
   h->smem = h->use_gws ? 0 : (size_t)tpb * ws_bytes;
   h->fn = fn;
   h->plain_fn = pfn;
+  h->use_cluster = false;
+  if (h->use_gws && h->uniform && team_is_default && h->opt.cluster_ctas != 1 && !has_implicit_desc(h)) {
+    dmpc_err ce = configure_cluster(h, maxK);
+    if (ce != DMPC_OK) return ce;
+  }
   return DMPC_OK;
 }
 
@@ -442,8 +526,20 @@ static KParams base_params(dmpc_handle* h) {
   return P;
 }
 
+// Launch the handle's kernel over n work items (the cluster form caps its clusters at n).
+static cudaError_t launch_items(dmpc_handle* h, KParams P, int n) {
+  if (h->use_cluster) {
+    P.cl_kc = h->cl_kc;
+    P.teams_per_block = 1;
+    const int ncl = std::max(1, std::min(h->cl_max, n));
+    return h->cl_fn(P, ncl * h->cl_ncta, h->cl_ncta, h->smem, h->stream);
+  }
+  const int grid = std::max(1, std::min(h->grid, (n + h->tpb - 1) / h->tpb));
+  return h->fn(P, grid, h->team * h->tpb, h->smem, h->stream);
+}
+
 static dmpc_err launch(dmpc_handle* h, const KParams& P) {
-  cudaError_t e = h->fn(P, h->grid, h->team * h->tpb, h->smem, h->stream);
+  cudaError_t e = launch_items(h, P, P.n_work);
   if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
   return DMPC_OK;
 }
@@ -836,8 +932,7 @@ extern "C" dmpc_err dmpc_solve_subset(dmpc_handle* h, const int* index, int n, c
   if (er != DMPC_OK || n == 0) return er;
   OPTIONAL_DEV(lam_out, "lam_out");
   P.lam_out = lam_out; P.status = status_out; P.pcg_iters = pcg_iters_out; P.alpha_hist = alpha_out;
-  const int grid = std::max(1, std::min(h->grid, (n + h->tpb - 1) / h->tpb));
-  cudaError_t e = h->fn(P, grid, h->team * h->tpb, h->smem, h->stream);
+  cudaError_t e = launch_items(h, P, n);
   if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
   h->have_solution = true;
   h->last_had_xref = x_ref != nullptr;
@@ -923,6 +1018,15 @@ extern "C" dmpc_err dmpc_get_tiling(const dmpc_handle* h, int* team_threads, int
   if (teams_per_block) *teams_per_block = h->tpb;
   if (grid) *grid = h->grid;
   if (smem_bytes) *smem_bytes = (long long)h->smem;
+  return DMPC_OK;
+}
+
+extern "C" dmpc_err dmpc_get_cluster(const dmpc_handle* h, int* ctas_per_cluster, int* knots_per_cta,
+                                     int* clusters) {
+  if (!h) return DMPC_E_ARG;
+  if (ctas_per_cluster) *ctas_per_cluster = h->use_cluster ? h->cl_ncta : 0;
+  if (knots_per_cta) *knots_per_cta = h->use_cluster ? h->cl_kc : 0;
+  if (clusters) *clusters = h->use_cluster ? h->cl_max : 0;
   return DMPC_OK;
 }
 

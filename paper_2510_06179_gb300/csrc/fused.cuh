@@ -94,6 +94,9 @@ constexpr int MS_BAD = 120;  // nonzero when a weight or parameter is not finite
 // [0,16) 1/Q, [16,24) 1/R, [24,40) 1/Q_T  (in doubles)
 constexpr int MS_DINV = 128;
 
+template <class M>
+struct ClRun;
+
 template <class M, int TEAM>
 struct Ctx {
   static constexpr int NX = M::NX, NU = M::NU, NZ = M::NX + M::NU;
@@ -108,6 +111,7 @@ struct Ctx {
   int status;
   int df_iters;  // PCG iterations of the current solve run in the double-float rescue (inspect output)
   bool exact;  // backward with the exact Hessian of the Lagrangian (Riccati solve), else Gauss-Newton
+  ClRun<M>* cl = nullptr;  // set when the OCP runs on a thread-block cluster (its PCG solves are distributed)
 
   __device__ __forceinline__ float* F(int off) const { return fb + off; }
   __device__ __forceinline__ double* Dp(int off) const { return db + off; }
@@ -2134,8 +2138,37 @@ __device__ __noinline__ int stage_pcg_warp_cg(Ctx<M, 32>& c) {
 }
 
 // PCG entry: the register-resident inner loop when one knot per lane fits (nx <= 6).
+}  // namespace dmpc
+#include "dpcg.cuh"
+namespace dmpc {
+
+// Leader side of the distributed PCG: hand the solve to every CTA of the cluster, take part in
+// it, and finish a stagnated solve with the double-float rescue from the global workspace.
+template <class M>
+__device__ __noinline__ int stage_pcg_cluster(Ctx<M, kClThreads>& c) {
+  ClRun<M>& r = *c.cl;
+  cl_command<M>(r, CL_PCG, c.ocp, c.K, c.T);
+  const ClResult res = cl_pcg<M>(r, *c.P, c.K, c.T, c.fb);
+  __threadfence();
+  int it = res.it;
+  if (r.broken) {
+    c.status |= ST_SYNC_TIMEOUT;
+    return it;
+  }
+  if (!res.converged) {
+    c.status |= ST_FP64_RESCUE;
+    const int d = stage_pcg_df<M, kClThreads>(c, res.eta0, c.P->opt.pcg_max_iters);
+    c.df_iters += d;
+    it += d;
+  }
+  return it;
+}
+
 template <class M, int TEAM>
 __device__ __forceinline__ int run_pcg(Ctx<M, TEAM>& c) {
+  if constexpr (kClusterPcg && TEAM == kClThreads && M::NX % kClRows == 0 && !is_implicit<M>::value) {
+    if (c.cl && !c.cl->broken) return stage_pcg_cluster<M>(c);
+  }
   if constexpr (M::NX <= 4) {
     if constexpr (TEAM == 32) {
       if (c.P->opt.pcg_variant == 1) {
@@ -2695,8 +2728,9 @@ __device__ __noinline__ void run_backward(Ctx<M, TEAM>& c) {
 }
 
 template <class M, int TEAM>
-__device__ void run_one(const KParams& P, int ocp, float* ws, int lane, int team_in_block) {
+__device__ void run_one(const KParams& P, int ocp, float* ws, int lane, int team_in_block, ClRun<M>* cl = nullptr) {
   Ctx<M, TEAM> c;
+  c.cl = cl;
   c.P = &P;
   c.o = P.ocps[ocp];
   c.ocp = ocp;
@@ -2739,5 +2773,35 @@ __global__ void __launch_bounds__(256, 1) fused_kernel(const __grid_constant__ K
   float* ws = P.use_gws ? P.gws + (size_t)gteam * P.ws_floats : smem + (size_t)tib * P.ws_floats;
   for (int w = gteam; w < P.n_work; w += nteams) dispatch<TEAM, Ms...>(P, P.order[w], ws, lane, tib);
 }
+
+#ifdef DMPC_CLUSTER_PCG
+// One cluster of CTAs per OCP (persistent over the work list: cluster g takes items g, g + G, ...).
+// CTA 0 runs the OCP from its global workspace slot; all CTAs run its PCG solves from their
+// shared memory.  Launched with a cluster dimension of 2..8 CTAs of kClThreads threads.
+template <class M>
+__global__ void __launch_bounds__(kClThreads, 1) fused_cluster_kernel(const __grid_constant__ KParams P) {
+  extern __shared__ __align__(16) float smem[];
+  ClRun<M> r;
+  r.init(smem, P.cl_kc);
+  if (threadIdx.x == 0) {
+    cl::bar_init(r.bar(0), r.ncta);
+    cl::bar_init(r.bar(1), r.ncta);
+    cl::bar_init(r.bar(2), 1);
+    cl::fence_bar_init();
+  }
+  __syncthreads();
+  cl::sync_all();
+  const int cid = (int)cl::id(), ncl = (int)cl::nclusters();
+  float* ws = P.gws + (size_t)cid * P.ws_floats;
+  if (r.rank == 0) {
+    for (int w = cid; w < P.n_work; w += ncl) run_one<M, kClThreads>(P, P.order[w], ws, threadIdx.x, 0, &r);
+    if (!r.broken) cl_command<M>(r, CL_EXIT, 0, 0, 0);
+  } else {
+    cl_follower<M>(r, P, ws);
+  }
+  __syncthreads();
+  cl::sync_all();
+}
+#endif
 
 }  // namespace dmpc

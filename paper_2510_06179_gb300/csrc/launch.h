@@ -41,6 +41,19 @@ DMPC_DECLARE_TEAMS(rigid_body)
 DMPC_DECLARE_TEAMS(attitude)
 DMPC_DECLARE_TEAMS(mixed)
 
+// Cluster kernel of one model (distributed PCG): launch with `ncta` CTAs per cluster and
+// `grid` CTAs in total; `max_clusters` returns how many such clusters fit on the device at once.
+typedef cudaError_t (*ClusterLaunchFn)(const KParams& P, int grid, int ncta, size_t smem, cudaStream_t s);
+typedef int (*ClusterOccFn)(int ncta, size_t smem);
+struct ClusterEntry {
+  int model, nx, nu;
+  ClusterLaunchFn fn;
+  ClusterOccFn max_clusters;
+};
+int register_cluster_rigid_body(ClusterEntry*);
+constexpr int kMaxClusterEntries = 8;
+int collect_cluster_entries(ClusterEntry* out);
+
 // Raise a kernel's dynamic shared-memory limit to at least `smem` bytes on the current device.
 // The attribute is per device, so the largest size set so far is kept per (kernel, device);
 // a mutex makes concurrent callers (different host threads or devices) safe.

@@ -74,6 +74,7 @@ struct KParams {
   float* gws;                // global per-team workspace (used when it does not fit in smem)
   int use_gws;
   int teams_per_block;
+  int cl_kc;                 // cluster launches: knot capacity of one CTA's shared-memory layout
 };
 
 }  // namespace dmpc

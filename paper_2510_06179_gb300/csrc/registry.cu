@@ -41,4 +41,10 @@ int collect_kernel_entries(KernelEntry* out) {
 #undef DMPC_COLLECT
   return n;
 }
+
+int collect_cluster_entries(ClusterEntry* out) {
+  int n = 0;
+  n += register_cluster_rigid_body(out + n);
+  return n;
+}
 }  // namespace dmpc

@@ -178,6 +178,12 @@ class OCPBatch:
             o += size
         return out
 
+    def get_cluster(self):
+        """Cluster form of the handle: CTAs per cluster, knots per CTA, clusters (all 0 when off)."""
+        v = [ctypes.c_int(), ctypes.c_int(), ctypes.c_int()]
+        _lib.check(self.lib.dmpc_get_cluster(self.h, *[ctypes.byref(x) for x in v]), self.h)
+        return dict(ctas_per_cluster=v[0].value, knots_per_cta=v[1].value, clusters=v[2].value)
+
     def set_tiling(self, team_threads, teams_per_block):
         _lib.check(self.lib.dmpc_set_tiling(self.h, team_threads, teams_per_block), self.h)
 

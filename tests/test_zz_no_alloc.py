@@ -77,8 +77,9 @@ def test_noalloc_global_workspace_branch_matches_regular_solve_and_oracle():
     lib = _lib.load()
     w = workloads.rigid_body_config(B=3, T=200, seed=21, sqp_iters=3)
     opts = dict(sqp_iters=w.sqp_iters, line_search=1, pcg_tol=1e-9, warm_start=0)
-    reg = OCPBatch((w.model, w.nx, w.nu, w.T, w.dt), batch=w.B, device="cuda:0", **opts)
-    assert reg.get_tiling()["smem_bytes"] == 0          # the regular path also runs it from global memory
+    # the regular path in its one-team form (no thread-block cluster) runs it from global memory too
+    reg = OCPBatch((w.model, w.nx, w.nu, w.T, w.dt), batch=w.B, device="cuda:0", cluster_ctas=1, **opts)
+    assert reg.get_tiling()["smem_bytes"] == 0
     x_s, th, xr = dev(w.x_s), dev(w.theta), dev(w.x_ref)
     ref = reg.solve(x_s, th, xr)
     torch.cuda.synchronize()
