@@ -67,6 +67,22 @@ __device__ __forceinline__ void st_f64(uint32_t a, double v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
 }
 
+// Asynchronous store into another CTA's shared memory that signals the mbarrier `bar` of that
+// CTA (both shared::cluster addresses) with its 4 or 8 bytes when it lands.
+__device__ __forceinline__ void st_async_f32(uint32_t a, float v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(a), "f"(v), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async_f64(uint32_t a, double v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];" ::"r"(a), "d"(v), "r"(bar)
+               : "memory");
+}
+// arrive on this CTA's mbarrier at `a`, announcing `bytes` of asynchronous stores for its phase
+__device__ __forceinline__ void arrive_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(a), "r"(bytes)
+               : "memory");
+}
+
 // mbarrier in this CTA's shared memory, expecting `count` arrivals per phase
 __device__ __forceinline__ void bar_init(uint32_t a, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");

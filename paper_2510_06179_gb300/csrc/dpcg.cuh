@@ -7,12 +7,16 @@
 // runs with every block resident on chip:
 //   - knot k's row of S p (and of Phi^-1 r) needs p_{k-1} and the product with block k+1; a CTA
 //     keeps the first block of the next CTA as a halo copy, and the owner of a boundary knot
-//     pushes the vector values its neighbours need into their shared memory (DSMEM stores)
-//     before the next all-reduce, so no extra synchronisation is needed for the halos;
+//     sends the vector values its neighbours need into their shared memory along with the next
+//     all-reduce, so the halos cost no extra synchronisation;
 //   - each of the two dot products of an iteration is an all-reduce: warp shuffles, one partial
-//     per warp, then every CTA stores its partial into a slot of every other CTA and arrives on
-//     that CTA's mbarrier; every CTA sums the slots in rank order, so all CTAs hold bitwise the
-//     same totals and take the same decisions;
+//     per warp, then every CTA stores its partial into a slot of every CTA with an asynchronous
+//     DSMEM store that completes bytes on the receiver's mbarrier (st.async), so a phase is done
+//     when all bytes it expects (partials and halo values) have landed; every CTA sums the slots
+//     in rank order, so all CTAs hold bitwise the same totals and take the same decisions;
+//   - the updates p = z + beta p and r = r - alpha y are applied where they are consumed (each
+//     thread forms the values of the three knots its block row reads, from double-buffered
+//     vectors), so an iteration synchronises only at its two all-reduces;
 //   - reliable updates evaluate the FP64 true residual gamma - H G^-1 H^T lambda from the
 //     factors (hp_apply's two passes, distributed the same way) and the stagnation test hands
 //     the solve back to the leader, which finishes it with the double-float rescue from global
@@ -38,20 +42,23 @@ constexpr bool kClusterPcg = false;
 #endif
 
 enum ClCommand : int { CL_PCG = 1, CL_EXIT = 2 };
+// mbarriers of a CTA: two for the all-reduce phases (alternating), the leader's command, and a
+// release barrier for the end of a solve (global-memory write-back)
+enum ClBar : int { CB_RED0 = 0, CB_RED1 = 1, CB_CMD = 2, CB_REL = 3 };
 
 // Shared-memory layout of one CTA of the cluster (float offsets unless noted).  KC = knot
-// capacity per CTA.  Blocks are knot-minor over KB = KC + 1 slots (slot KC + ... : the next
-// CTA's first knot); vectors over KV = KC + 2 slots: slot 0 = the previous CTA's last knot,
-// slots 1..nk = own knots, slot nk + 1 = the next CTA's first knot.
+// capacity per CTA.  Blocks are knot-minor over KB = KC + 1 slots (slot nk holds the next CTA's
+// first knot); vectors over KV = KC + 2 slots (slot 0 and nk + 1 are halo slots, own knots at
+// 1..nk).  P and R are double-buffered.
 struct ClLayout {
   int KC, KB, KV;
   int D, O, Pd, Po, A, Bm;   // float blocks
-  int Pv, R, Y, Z, DL;       // float vectors
+  int Pv[2], R[2], Y, Z, DL; // float vectors
   int rh, yh, zh, ph;        // halo staging, [side][NX]: side 0 = previous CTA, 1 = next CTA
   int misc;                  // copy of the OCP's scalars (weights, reciprocals)
   int wpart, slots;          // all-reduce scratch: 2 x warps x kClNV, 2 x kClMaxCtas x kClNV
   int job;                   // command words written by the leader
-  int bars;                  // mbarriers (8 bytes each): all-reduce 0, 1, command
+  int bars;                  // four mbarriers (ClBar)
   int dbase;                 // float offset of the double region
   int LP, G, WX, WU;         // double vectors (offsets in doubles from dbase)
   int total;
@@ -71,8 +78,10 @@ __host__ __device__ inline ClLayout cl_layout(int nx, int nu, int kc) {
   S.A = f; f += b;
   S.Bm = f; f += nx * nu * S.KB;
   const int v = nx * S.KV;
-  S.Pv = f; f += v;
-  S.R = f; f += v;
+  S.Pv[0] = f; f += v;
+  S.Pv[1] = f; f += v;
+  S.R[0] = f; f += v;
+  S.R[1] = f; f += v;
   S.Y = f; f += v;
   S.Z = f; f += v;
   S.DL = f; f += v;
@@ -112,6 +121,7 @@ struct ClRun {
   int tid;
   int phase;        // all-reduce phase counter
   uint32_t cmd_par; // parity of the next command phase (followers)
+  uint32_t rel_par; // parity of the next release-barrier phase
   bool broken;      // a wait ran out: no more waiting in this CTA
   // current OCP
   int K, T, KC, k0, nk, kl, r0;
@@ -126,11 +136,11 @@ struct ClRun {
   __device__ __forceinline__ double rinv(int i) const {
     return reinterpret_cast<const double*>(sm + S.misc + MS_DINV)[16 + i];
   }
-  // shared::cluster address of element `off` (floats) of CTA `r`'s shared memory
-  __device__ __forceinline__ uint32_t remote(int off, uint32_t r) const { return cl::map(cl::saddr(sm + off), r); }
-  __device__ __forceinline__ uint32_t remote_d(int doff, uint32_t r) const {
-    return cl::map(cl::saddr(dm + doff), r);
-  }
+  // shared::cluster address of float `off` (or double `doff`) of CTA `q`'s shared memory
+  __device__ __forceinline__ uint32_t remote(int off, uint32_t q) const { return cl::map(cl::saddr(sm + off), q); }
+  __device__ __forceinline__ uint32_t remote_d(int doff, uint32_t q) const { return cl::map(cl::saddr(dm + doff), q); }
+  // the all-reduce mbarrier of the coming phase in CTA q
+  __device__ __forceinline__ uint32_t red_bar(uint32_t q) const { return cl::map(bar(phase & 1), q); }
 
   __device__ void init(float* smem, int kc) {
     sm = smem;
@@ -141,6 +151,7 @@ struct ClRun {
     tid = threadIdx.x;
     phase = 0;
     cmd_par = 0;
+    rel_par = 0;
     broken = false;
   }
   // knot partition of an OCP with K knots over the cluster's CTAs
@@ -157,13 +168,18 @@ struct ClRun {
     has_prev = nk > 0 && k0 > 0;
     has_next = nk > 0 && k0 + nk < K;
   }
+  // bytes of halo values this CTA receives in a phase where each existing neighbour sends
+  // `per_side` bytes
+  __device__ __forceinline__ uint32_t halo_bytes(uint32_t per_side) const {
+    return per_side * ((has_prev ? 1u : 0u) + (has_next ? 1u : 0u));
+  }
 };
 
 // Sum NV values over every thread of every CTA of the cluster; all threads of all CTAs receive
-// bitwise the same totals.  Also a cluster-wide barrier: shared-memory and global writes made
-// before it by any thread of the cluster are visible after it.
+// bitwise the same totals.  halo_rx: bytes of halo values other CTAs send to this one in the same
+// phase (their st.async stores signal the same mbarrier), which are visible after the call.
 template <class M, int NV>
-__device__ __forceinline__ void cl_sum(ClRun<M>& r, float (&v)[NV]) {
+__device__ __forceinline__ void cl_sum(ClRun<M>& r, float (&v)[NV], uint32_t halo_rx) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
@@ -187,10 +203,11 @@ __device__ __forceinline__ void cl_sum(ClRun<M>& r, float (&v)[NV]) {
       for (int j = 0; j < NV; ++j) s[j] += wp[q * kClNV + j];
     }
     const uint32_t dst = r.remote(r.S.slots + b * kClMaxCtas * kClNV + (int)r.rank * kClNV, (uint32_t)r.tid);
+    const uint32_t rb = r.red_bar((uint32_t)r.tid);
 #pragma unroll
-    for (int j = 0; j < NV; ++j) cl::st_f32(dst + 4u * (uint32_t)j, s[j]);
-    cl::arrive_remote(cl::map(r.bar(b), (uint32_t)r.tid));
+    for (int j = 0; j < NV; ++j) cl::st_async_f32(dst + 4u * (uint32_t)j, s[j], rb);
   }
+  if (r.tid == 0 && !r.broken) cl::arrive_expect_tx(r.bar(b), r.ncta * NV * 4u + halo_rx);
   bool ok = r.broken ? false : cl::wait(r.bar(b), par, kClWaitNs);
   ok = __syncthreads_and(ok) != 0;
   if (!ok) r.broken = true;
@@ -204,45 +221,55 @@ __device__ __forceinline__ void cl_sum(ClRun<M>& r, float (&v)[NV]) {
 }
 
 template <class M>
-__device__ __forceinline__ void cl_barrier(ClRun<M>& r) {
+__device__ __forceinline__ void cl_barrier(ClRun<M>& r, uint32_t halo_rx) {
   float d[1] = {0.f};
-  cl_sum<M, 1>(r, d);
+  cl_sum<M, 1>(r, d, halo_rx);
 }
 
-// Push this thread's rows of a boundary knot's values into the staging arrays of the
-// neighbouring CTAs (side 1 of the previous CTA, side 0 of the next CTA).
+// Release barrier over the cluster: every thread's earlier writes (global memory included) are
+// visible to every thread of the cluster after it.
+template <class M>
+__device__ __forceinline__ void cl_release_barrier(ClRun<M>& r) {
+  __syncthreads();
+  if (r.tid < (int)r.ncta && !r.broken) cl::arrive_remote(cl::map(r.bar(CB_REL), (uint32_t)r.tid));
+  bool ok = true;
+  if (r.tid == 0) ok = r.broken ? false : cl::wait(r.bar(CB_REL), r.rel_par, kClWaitNs);
+  ok = __syncthreads_and(ok) != 0;
+  if (!ok) r.broken = true;
+  r.rel_par ^= 1u;
+}
+
+// Send this thread's rows of a boundary knot's values (a, b) into the staging arrays of the
+// neighbouring CTAs (side 1 of the previous CTA, side 0 of the next CTA) for the coming phase.
 template <class M>
 __device__ __forceinline__ void cl_push_pair(ClRun<M>& r, int st_a, int st_b, const float* a, const float* b) {
   constexpr int NX = M::NX;
-  if (!r.act) return;
+  if (!r.act || r.broken) return;
   if (r.kl == 0 && r.has_prev) {
-    const uint32_t da = r.remote(st_a + NX + r.r0, r.rank - 1), db = r.remote(st_b + NX + r.r0, r.rank - 1);
+    const uint32_t q = r.rank - 1, rb = r.red_bar(q);
+    const uint32_t da = r.remote(st_a + NX + r.r0, q), db = r.remote(st_b + NX + r.r0, q);
 #pragma unroll
-    for (int q = 0; q < kClRows; ++q) { cl::st_f32(da + 4u * q, a[q]); cl::st_f32(db + 4u * q, b[q]); }
+    for (int i = 0; i < kClRows; ++i) { cl::st_async_f32(da + 4u * i, a[i], rb); cl::st_async_f32(db + 4u * i, b[i], rb); }
   }
   if (r.kl == r.nk - 1 && r.has_next) {
-    const uint32_t da = r.remote(st_a + r.r0, r.rank + 1), db = r.remote(st_b + r.r0, r.rank + 1);
+    const uint32_t q = r.rank + 1, rb = r.red_bar(q);
+    const uint32_t da = r.remote(st_a + r.r0, q), db = r.remote(st_b + r.r0, q);
 #pragma unroll
-    for (int q = 0; q < kClRows; ++q) { cl::st_f32(da + 4u * q, a[q]); cl::st_f32(db + 4u * q, b[q]); }
+    for (int i = 0; i < kClRows; ++i) { cl::st_async_f32(da + 4u * i, a[i], rb); cl::st_async_f32(db + 4u * i, b[i], rb); }
   }
 }
 
 // Rows [r0, r0 + kClRows) of the symmetric block-tridiagonal row of knot kl:
-// out = Md_k v_k + Mo_k v_{k-1} + Mo_{k+1}^T v_{k+1} (block slots kl and kl + 1, vector slots
-// kl, kl + 1, kl + 2; missing neighbours are zero blocks and zero halos).
-template <class M, class V>
-__device__ __forceinline__ void cl_btmv_rows(const ClRun<M>& r, int md, int mo, const V* v, float (&out)[kClRows]) {
+// out = Md_k v_k + Mo_k v_{k-1} + Mo_{k+1}^T v_{k+1} (block slots kl and kl + 1; missing
+// neighbours are zero blocks and zero vectors).
+template <class M>
+__device__ __forceinline__ void cl_block_rows(const ClRun<M>& r, int md, int mo, const float (&vm)[M::NX],
+                                              const float (&vc)[M::NX], const float (&vp)[M::NX],
+                                              float (&out)[kClRows]) {
   constexpr int NX = M::NX;
-  const int KB = r.S.KB, KV = r.S.KV, kl = r.kl;
+  const int KB = r.S.KB, kl = r.kl;
   const float* Md = r.F(md);
   const float* Mo = r.F(mo);
-  float vm[NX], vc[NX], vp[NX];
-#pragma unroll
-  for (int j = 0; j < NX; ++j) {
-    vm[j] = (float)v[j * KV + kl];
-    vc[j] = (float)v[j * KV + kl + 1];
-    vp[j] = (float)v[j * KV + kl + 2];
-  }
 #pragma unroll
   for (int q = 0; q < kClRows; ++q) {
     const int i = r.r0 + q;
@@ -257,33 +284,96 @@ __device__ __forceinline__ void cl_btmv_rows(const ClRun<M>& r, int md, int mo, 
   }
 }
 
-// Z = Phi^-1 R on this thread's rows; returns its share of R^T Z and pushes the boundary knots'
-// z and p to the neighbours (for their p halo after the next all-reduce).
+// Values x = a + s b of knots kl - 1, kl, kl + 1 (vector arrays a, b over the vector slots; a
+// halo knot from the staging arrays ha, hb of its side, which stay zero when the side has no
+// neighbour).  The source of each knot is chosen by pointer, so every value costs two loads.
 template <class M>
-__device__ __forceinline__ float cl_precond(ClRun<M>& r) {
+__device__ __forceinline__ void cl_gather(const ClRun<M>& r, const float* a, const float* b, float s, const float* ha,
+                                          const float* hb, float (&xm)[M::NX], float (&xc)[M::NX],
+                                          float (&xp)[M::NX]) {
+  constexpr int NX = M::NX;
+  const int KV = r.S.KV, sl = r.kl + 1;
+  const bool first = r.kl == 0, last = r.kl == r.nk - 1;
+  const float* am = first ? ha : a + sl - 1;
+  const float* bm = first ? hb : b + sl - 1;
+  const float* ap = last ? ha + NX : a + sl + 1;
+  const float* bp = last ? hb + NX : b + sl + 1;
+  const int sm_ = first ? 1 : KV, sp_ = last ? 1 : KV;
+#pragma unroll
+  for (int j = 0; j < NX; ++j) {
+    xc[j] = fmaf(s, b[j * KV + sl], a[j * KV + sl]);
+    xm[j] = fmaf(s, bm[j * sm_], am[j * sm_]);
+    xp[j] = fmaf(s, bp[j * sp_], ap[j * sp_]);
+  }
+}
+
+// First half of an iteration: p = z + beta p_old (formed where read), own rows of p into
+// Pv[pnew], y = S p rows into Y; returns this thread's share of p^T y and sends the boundary
+// knots' r (current, R[rcur]) and y to the neighbours.
+template <class M>
+__device__ __forceinline__ float cl_step_sp(ClRun<M>& r, int pold, int pnew, int rcur, float beta) {
   constexpr int NX = M::NX;
   if (!r.act) return 0.f;
-  const int KV = r.S.KV, s = r.kl + 1;
-  float z[kClRows], pv[kClRows];
-  cl_btmv_rows<M, float>(r, r.S.Pd, r.S.Po, r.F(r.S.R), z);
+  const int KV = r.S.KV, sl = r.kl + 1;
+  float pm[NX], pc[NX], pp[NX], y[kClRows], rv[kClRows];
+  cl_gather<M>(r, r.F(r.S.Z), r.F(r.S.Pv[pold]), beta, r.F(r.S.zh), r.F(r.S.ph), pm, pc, pp);
+  cl_block_rows<M>(r, r.S.D, r.S.O, pm, pc, pp, y);
+  float v = 0.f;
+#pragma unroll
+  for (int q = 0; q < kClRows; ++q) {
+    const int i = r.r0 + q;
+    r.F(r.S.Pv[pnew])[i * KV + sl] = pc[i];
+    r.F(r.S.Y)[i * KV + sl] = y[q];
+    v = fmaf(pc[i], y[q], v);
+    rv[q] = r.F(r.S.R[rcur])[i * KV + sl];
+  }
+  cl_push_pair<M>(r, r.S.rh, r.S.yh, rv, y);
+  return v;
+}
+
+// Second half: r_new = r - alpha y (formed where read; own rows into R[rnew] and dl += alpha p
+// when UPD), z = Phi^-1 r_new rows into Z; returns the share of r_new^T z and sends the boundary
+// knots' z and p (Pv[pcur]) to the neighbours.  Without UPD r is R[rcur] as it stands (after a
+// true-residual replacement; halos from the staging with y = 0).
+template <class M, bool UPD>
+__device__ __forceinline__ float cl_step_pc(ClRun<M>& r, int rcur, int rnew, int pcur, float alpha) {
+  constexpr int NX = M::NX;
+  if (!r.act) return 0.f;
+  const int KV = r.S.KV, sl = r.kl + 1;
+  float rm[NX], rc[NX], rp[NX], z[kClRows], pv[kClRows];
+  const float* Rc = r.F(r.S.R[rcur]);
+  if (UPD) cl_gather<M>(r, Rc, r.F(r.S.Y), -alpha, r.F(r.S.rh), r.F(r.S.yh), rm, rc, rp);
+  else cl_gather<M>(r, Rc, Rc, 0.f, r.F(r.S.rh), r.F(r.S.rh), rm, rc, rp);
+  cl_block_rows<M>(r, r.S.Pd, r.S.Po, rm, rc, rp, z);
   float e = 0.f;
 #pragma unroll
   for (int q = 0; q < kClRows; ++q) {
     const int i = r.r0 + q;
-    r.F(r.S.Z)[i * KV + s] = z[q];
-    e = fmaf(r.F(r.S.R)[i * KV + s], z[q], e);
-    pv[q] = r.F(r.S.Pv)[i * KV + s];
+    pv[q] = r.F(r.S.Pv[pcur])[i * KV + sl];
+    if (UPD) {
+      r.F(r.S.R[rnew])[i * KV + sl] = rc[i];
+      r.F(r.S.DL)[i * KV + sl] = fmaf(alpha, pv[q], r.F(r.S.DL)[i * KV + sl]);
+    }
+    r.F(r.S.Z)[i * KV + sl] = z[q];
+    e = fmaf(rc[i], z[q], e);
   }
-  (void)NX;
   cl_push_pair<M>(r, r.S.zh, r.S.ph, z, pv);
   return e;
 }
 
-// FP64 true residual R = gamma - H G^-1 H^T LP on the own knots (hp_apply's two passes), leaving
-// WX, WU = H^T LP; halos: the next CTA's first LP (pushed when push_lp, else already present),
-// the previous CTA's last WX, WU and both neighbours' new R (pushed).
+// FP64 true residual R[rb] = gamma - H G^-1 H^T LP on the own knots (hp_apply's two passes),
+// leaving WX, WU = H^T LP; halos: the next CTA's first LP (sent when push_lp, else already in
+// place), the previous CTA's last WX, WU, and both neighbours' new R (sent into the staging with
+// y = 0).  Three phases (two without push_lp).
+struct ClSync {
+  int phase;
+  bool broken;
+};
+
+// r is taken by value (so that the caller's copy stays in registers); returns its all-reduce
+// state after the call.
 template <class M>
-__device__ void cl_hp_residual(ClRun<M>& r, bool push_lp) {
+__device__ __noinline__ ClSync cl_hp_residual(ClRun<M> r, bool push_lp, int rb) {
   constexpr int NX = M::NX, NU = M::NU;
   const int KB = r.S.KB, KV = r.S.KV, kl = r.kl, s = kl + 1;
   const int k = r.k0 + kl;
@@ -294,49 +384,46 @@ __device__ void cl_hp_residual(ClRun<M>& r, bool push_lp) {
   const float* A = r.F(r.S.A);
   const float* Bm = r.F(r.S.Bm);
   if (push_lp) {
-    if (r.act && kl == 0 && r.has_prev) {
+    if (r.act && kl == 0 && r.has_prev && !r.broken) {
+      const uint32_t q = r.rank - 1, rbar = r.red_bar(q);
 #pragma unroll
-      for (int q = 0; q < kClRows; ++q) {
-        const int i = r.r0 + q;
-        cl::st_f64(r.remote_d(r.S.LP + i * KV + r.KC + 1, r.rank - 1), LP[i * KV + s]);
+      for (int j = 0; j < kClRows; ++j) {
+        const int i = r.r0 + j;
+        cl::st_async_f64(r.remote_d(r.S.LP + i * KV + r.KC + 1, q), LP[i * KV + s], rbar);
       }
     }
-    cl_barrier<M>(r);
+    cl_barrier<M>(r, r.has_next ? 8u * NX : 0u);
   }
   // pass 1: w = H^T LP at knot k (A_k, B_k at block slot kl + 1, stored as A_k + I)
   if (r.act) {
     double ln[NX];
 #pragma unroll
     for (int j = 0; j < NX; ++j) ln[j] = (k < r.T) ? LP[j * KV + s + 1] : 0.0;
-    double wx[kClRows];
+    const bool send = kl == r.nk - 1 && r.has_next && !r.broken;
+    const uint32_t q = r.rank + 1, rbar = send ? r.red_bar(q) : 0u;
 #pragma unroll
-    for (int q = 0; q < kClRows; ++q) {
-      const int i = r.r0 + q;
+    for (int j = 0; j < kClRows; ++j) {
+      const int i = r.r0 + j;
       double acc = LP[i * KV + s];
       if (k < r.T) {
         acc -= ln[i];
 #pragma unroll
-        for (int j = 0; j < NX; ++j) acc += (double)A[(j * NX + i) * KB + kl + 1] * ln[j];
+        for (int c = 0; c < NX; ++c) acc += (double)A[(c * NX + i) * KB + kl + 1] * ln[c];
       }
-      wx[q] = acc;
       WX[i * KV + s] = acc;
+      if (send) cl::st_async_f64(r.remote_d(r.S.WX + i * KV + 0, q), acc, rbar);
     }
     for (int u = r.r0 / kClRows; u < NU; u += r.RG) {
       double acc = 0.0;
       if (k < r.T) {
 #pragma unroll
-        for (int j = 0; j < NX; ++j) acc += (double)Bm[(j * NU + u) * KB + kl + 1] * ln[j];
+        for (int c = 0; c < NX; ++c) acc += (double)Bm[(c * NU + u) * KB + kl + 1] * ln[c];
       }
       WU[u * KV + s] = acc;
-      if (kl == r.nk - 1 && r.has_next) cl::st_f64(r.remote_d(r.S.WU + u * KV + 0, r.rank + 1), acc);
-    }
-    if (kl == r.nk - 1 && r.has_next) {
-#pragma unroll
-      for (int q = 0; q < kClRows; ++q)
-        cl::st_f64(r.remote_d(r.S.WX + (r.r0 + q) * KV + 0, r.rank + 1), wx[q]);
+      if (send) cl::st_async_f64(r.remote_d(r.S.WU + u * KV + 0, q), acc, rbar);
     }
   }
-  cl_barrier<M>(r);
+  cl_barrier<M>(r, r.has_prev ? 8u * (NX + NU) : 0u);
   // pass 2: (H G^-1 w)_k on this thread's rows, then R = gamma - that
   if (r.act) {
     float rv[kClRows], zero[kClRows];
@@ -348,30 +435,31 @@ __device__ void cl_hp_residual(ClRun<M>& r, bool push_lp) {
       for (int j = 0; j < NU; ++j) vu[j] = WU[j * KV + s - 1] * r.rinv(j);
     }
 #pragma unroll
-    for (int q = 0; q < kClRows; ++q) {
-      const int i = r.r0 + q;
+    for (int j = 0; j < kClRows; ++j) {
+      const int i = r.r0 + j;
       double acc = WX[i * KV + s] * r.qinv(k, i);
       if (k > 0) {
         acc -= vx[i];
 #pragma unroll
-        for (int j = 0; j < NX; ++j) acc += (double)A[(i * NX + j) * KB + kl] * vx[j];
+        for (int c = 0; c < NX; ++c) acc += (double)A[(i * NX + c) * KB + kl] * vx[c];
 #pragma unroll
-        for (int j = 0; j < NU; ++j) acc += (double)Bm[(i * NU + j) * KB + kl] * vu[j];
+        for (int c = 0; c < NU; ++c) acc += (double)Bm[(i * NU + c) * KB + kl] * vu[c];
       }
-      rv[q] = (float)(G[i * KV + s] - acc);
-      r.F(r.S.R)[i * KV + s] = rv[q];
-      zero[q] = 0.f;
+      rv[j] = (float)(G[i * KV + s] - acc);
+      r.F(r.S.R[rb])[i * KV + s] = rv[j];
+      zero[j] = 0.f;
     }
     cl_push_pair<M>(r, r.S.rh, r.S.yh, rv, zero);
   }
-  cl_barrier<M>(r);
-  // R halos from the pushed values
-  if (r.tid < 2 * NX) {
-    const int side = r.tid / NX, i = r.tid % NX;
-    if (side == 0 ? r.has_prev : r.has_next)
-      r.F(r.S.R)[i * KV + (side == 0 ? 0 : r.nk + 1)] = r.F(r.S.rh)[side * NX + i];
-  }
-  __syncthreads();
+  cl_barrier<M>(r, r.halo_bytes(8u * NX));
+  return ClSync{r.phase, r.broken};
+}
+
+template <class M>
+__device__ __forceinline__ void cl_true_residual(ClRun<M>& r, bool push_lp, int rb) {
+  const ClSync st = cl_hp_residual<M>(r, push_lp, rb);
+  r.phase = st.phase;
+  r.broken = st.broken;
 }
 
 struct ClResult {
@@ -384,7 +472,21 @@ struct ClResult {
 // workspace (leader's layout L).  On return LP (the solution) and WX, WU (= H^T LP) are back in
 // the global workspace.
 template <class M>
-__device__ ClResult cl_pcg(ClRun<M>& r, const KParams& P, int K, int T, float* ws) {
+__device__ __forceinline__ ClResult cl_pcg_body(ClRun<M>& r, const KParams& P, int K, int T, float* ws);
+
+// Works on a register copy of the CTA's state and writes back what the solve changed.
+template <class M>
+__device__ __forceinline__ ClResult cl_pcg(ClRun<M>& rin, const KParams& P, int K, int T, float* ws) {
+  ClRun<M> r = rin;
+  const ClResult res = cl_pcg_body<M>(r, P, K, T, ws);
+  rin.phase = r.phase;
+  rin.rel_par = r.rel_par;
+  rin.broken = r.broken;
+  return res;
+}
+
+template <class M>
+__device__ __forceinline__ ClResult cl_pcg_body(ClRun<M>& r, const KParams& P, int K, int T, float* ws) {
   constexpr int NX = M::NX, NU = M::NU;
   ClResult res{0, false, 0.f};
   r.bind(K, T);
@@ -415,8 +517,10 @@ __device__ ClResult cl_pcg(ClRun<M>& r, const KParams& P, int K, int T, float* w
       r.Dd(r.S.LP)[idx] = in ? __ldcg(wd + L.d_lamp + i * KP + k) : 0.0;
       r.Dd(r.S.G)[idx] = in ? __ldcg(wd + L.d_gam + i * KP + k) : 0.0;
       r.Dd(r.S.WX)[idx] = 0.0;
-      r.F(r.S.Pv)[idx] = 0.f;
-      r.F(r.S.R)[idx] = 0.f;
+      r.F(r.S.Pv[0])[idx] = 0.f;
+      r.F(r.S.Pv[1])[idx] = 0.f;
+      r.F(r.S.R[0])[idx] = 0.f;
+      r.F(r.S.R[1])[idx] = 0.f;
       r.F(r.S.Y)[idx] = 0.f;
       r.F(r.S.Z)[idx] = 0.f;
       r.F(r.S.DL)[idx] = 0.f;
@@ -429,84 +533,51 @@ __device__ ClResult cl_pcg(ClRun<M>& r, const KParams& P, int K, int T, float* w
   const float tol2 = P.opt.pcg_tol * P.opt.pcg_tol;
   const float dl2 = P.opt.ru_delta * P.opt.ru_delta;
   const int maxit = P.opt.pcg_max_iters;
-  float* Pv = r.F(r.S.Pv);
-  float* R = r.F(r.S.R);
-  float* Y = r.F(r.S.Y);
-  float* Z = r.F(r.S.Z);
-  float* DL = r.F(r.S.DL);
+  const uint32_t pair_rx = r.halo_bytes(8u * NX);  // two vectors of NX floats from each neighbour
   double* LP = r.Dd(r.S.LP);
+  float* DL = r.F(r.S.DL);
   const int s = r.kl + 1;
+  int pb = 0, rb = 0;  // current buffers of p (holds the previous p until the next step) and r
 
-  // true residual of the initial guess (its next-CTA LP halo came from global memory)
-  cl_hp_residual<M>(r, false);
+  // true residual of the initial guess (its next-CTA LP halo came from global memory), z, eta,
+  // eta_0 = gamma^T Phi^-1 gamma from the FP32-rounded gamma
+  cl_true_residual<M>(r, false, rb);
   float e0[2] = {0.f, 0.f};
+  e0[0] = cl_step_pc<M, false>(r, rb, rb, pb, 0.f);
   if (r.act) {
-    e0[0] = cl_precond<M>(r);
-    float gt[kClRows];
-    cl_btmv_rows<M, double>(r, r.S.Pd, r.S.Po, r.Dd(r.S.G), gt);
+    float gm[NX], gc[NX], gp[NX], gt[kClRows];
+    const double* G = r.Dd(r.S.G);
 #pragma unroll
-    for (int q = 0; q < kClRows; ++q) e0[1] = fmaf((float)r.Dd(r.S.G)[(r.r0 + q) * KV + s], gt[q], e0[1]);
+    for (int j = 0; j < NX; ++j) {
+      gm[j] = (float)G[j * KV + s - 1];
+      gc[j] = (float)G[j * KV + s];
+      gp[j] = (float)G[j * KV + s + 1];
+    }
+    cl_block_rows<M>(r, r.S.Pd, r.S.Po, gm, gc, gp, gt);
+#pragma unroll
+    for (int q = 0; q < kClRows; ++q) e0[1] = fmaf(gc[r.r0 + q], gt[q], e0[1]);
   }
-  cl_sum<M, 2>(r, e0);
+  cl_sum<M, 2>(r, e0, pair_rx);
   float eta = e0[0];
   const float eta0 = e0[1];
   res.eta0 = eta0;
-  // p = z (beta = 0): own rows and halos
-  auto update_p = [&](float beta) {
-    if (r.tid < 2 * NX) {
-      const int side = r.tid / NX, i = r.tid % NX;
-      if (side == 0 ? r.has_prev : r.has_next)
-        Pv[i * KV + (side == 0 ? 0 : nk + 1)] = fmaf(beta, r.F(r.S.ph)[side * NX + i], r.F(r.S.zh)[side * NX + i]);
-    }
-    if (r.act) {
-#pragma unroll
-      for (int q = 0; q < kClRows; ++q) {
-        const int i = r.r0 + q;
-        Pv[i * KV + s] = fmaf(beta, Pv[i * KV + s], Z[i * KV + s]);
-      }
-    }
-    __syncthreads();
-  };
-  update_p(0.f);
+  float beta = 0.f;  // p = z for the first direction (the old p is zero)
   float eta_ref = eta, eta_true = eta;
   int it = 0, stall = 0;
   bool converged = !(eta > tol2 * eta0);
   bool folded = true;
   while (!converged && it < maxit && !r.broken) {
-    // y = S p, v = p^T y; boundary knots push their r and y for the neighbours' r halo
-    float v[1] = {0.f};
-    if (r.act) {
-      float y[kClRows], rv[kClRows];
-      cl_btmv_rows<M, float>(r, r.S.D, r.S.O, Pv, y);
-#pragma unroll
-      for (int q = 0; q < kClRows; ++q) {
-        const int i = r.r0 + q;
-        Y[i * KV + s] = y[q];
-        v[0] = fmaf(Pv[i * KV + s], y[q], v[0]);
-        rv[q] = R[i * KV + s];
-      }
-      cl_push_pair<M>(r, r.S.rh, r.S.yh, rv, y);
-    }
-    cl_sum<M, 1>(r, v);
+    // y = S p, v = p^T y
+    float v[1] = {cl_step_sp<M>(r, pb, pb ^ 1, rb, beta)};
+    pb ^= 1;
+    cl_sum<M, 1>(r, v, pair_rx);
     if (!(v[0] > 0.f) || !isfinite(v[0])) break;
     const float alpha = eta / v[0];
-    if (r.act) {
-#pragma unroll
-      for (int q = 0; q < kClRows; ++q) {
-        const int i = r.r0 + q;
-        DL[i * KV + s] = fmaf(alpha, Pv[i * KV + s], DL[i * KV + s]);
-        R[i * KV + s] = fmaf(-alpha, Y[i * KV + s], R[i * KV + s]);
-      }
-    }
-    if (r.tid < 2 * NX) {
-      const int side = r.tid / NX, i = r.tid % NX;
-      if (side == 0 ? r.has_prev : r.has_next)
-        R[i * KV + (side == 0 ? 0 : nk + 1)] = fmaf(-alpha, r.F(r.S.yh)[side * NX + i], r.F(r.S.rh)[side * NX + i]);
-    }
+    // r -= alpha y, dl += alpha p, z = Phi^-1 r, eta = r^T z
+    float e1[1] = {cl_step_pc<M, true>(r, rb, rb ^ 1, pb, alpha)};
+    rb ^= 1;
     folded = false;
-    __syncthreads();
-    float e1[1] = {cl_precond<M>(r)};
-    cl_sum<M, 1>(r, e1);
+    cl_sum<M, 1>(r, e1, pair_rx);
     float eta_new = e1[0];
     ++it;
     if (eta_new < dl2 * eta_ref || !(eta_new > tol2 * eta0) || it >= maxit || !isfinite(eta_new)) {
@@ -520,9 +591,9 @@ __device__ ClResult cl_pcg(ClRun<M>& r, const KParams& P, int K, int T, float* w
         }
       }
       folded = true;
-      cl_hp_residual<M>(r, true);
-      float e2[1] = {cl_precond<M>(r)};
-      cl_sum<M, 1>(r, e2);
+      cl_true_residual<M>(r, true, rb);
+      float e2[1] = {cl_step_pc<M, false>(r, rb, rb, pb, 0.f)};
+      cl_sum<M, 1>(r, e2, pair_rx);
       eta_new = e2[0];
       eta_ref = eta_new;
       if (!(eta_new > tol2 * eta0)) { converged = true; break; }
@@ -535,9 +606,8 @@ __device__ ClResult cl_pcg(ClRun<M>& r, const KParams& P, int K, int T, float* w
       eta_true = eta_new;
       if (it >= maxit) break;
     }
-    const float beta = eta_new / eta;
+    beta = eta_new / eta;
     eta = eta_new;
-    update_p(beta);
   }
   if (!folded && !r.broken) {
     if (r.act) {
@@ -547,7 +617,7 @@ __device__ ClResult cl_pcg(ClRun<M>& r, const KParams& P, int K, int T, float* w
         LP[i * KV + s] += (double)DL[i * KV + s];
       }
     }
-    cl_hp_residual<M>(r, true);
+    cl_true_residual<M>(r, true, rb);
   }
   // own knots of LP, WX, WU back to the global workspace
   if (!r.broken) {
@@ -562,7 +632,7 @@ __device__ ClResult cl_pcg(ClRun<M>& r, const KParams& P, int K, int T, float* w
       gd[L.d_wu + i * KP + k0 + j] = r.Dd(r.S.WU)[i * KV + j + 1];
     }
   }
-  cl_barrier<M>(r);
+  cl_release_barrier<M>(r);
   res.it = it;
   res.converged = converged && !r.broken;
   return res;
@@ -578,14 +648,15 @@ __device__ void cl_command(ClRun<M>& r, int cmd, int ocp, int K, int T) {
     job[0] = cmd; job[1] = ocp; job[2] = K; job[3] = T;
   }
   __syncthreads();
-  if (r.tid >= 1 && r.tid < (int)r.ncta && !r.broken) cl::arrive_remote(cl::map(r.bar(2), (uint32_t)r.tid));
+  if (r.tid >= 1 && r.tid < (int)r.ncta && !r.broken) cl::arrive_remote(cl::map(r.bar(CB_CMD), (uint32_t)r.tid));
 }
 
 // Other CTAs: run the leader's PCG commands until it sends CL_EXIT (or a wait runs out).
 template <class M>
 __device__ void cl_follower(ClRun<M>& r, const KParams& P, float* ws) {
   while (!r.broken) {
-    bool ok = cl::wait(r.bar(2), r.cmd_par, kClWaitNs);
+    bool ok = true;
+    if (r.tid == 0) ok = cl::wait(r.bar(CB_CMD), r.cmd_par, kClWaitNs);
     ok = __syncthreads_and(ok) != 0;
     if (!ok) { r.broken = true; break; }
     r.cmd_par ^= 1u;

@@ -2784,9 +2784,10 @@ __global__ void __launch_bounds__(kClThreads, 1) fused_cluster_kernel(const __gr
   ClRun<M> r;
   r.init(smem, P.cl_kc);
   if (threadIdx.x == 0) {
-    cl::bar_init(r.bar(0), r.ncta);
-    cl::bar_init(r.bar(1), r.ncta);
-    cl::bar_init(r.bar(2), 1);
+    cl::bar_init(r.bar(CB_RED0), 1);   // one local arrival per phase; the data completes its bytes
+    cl::bar_init(r.bar(CB_RED1), 1);
+    cl::bar_init(r.bar(CB_CMD), 1);    // the leader's command
+    cl::bar_init(r.bar(CB_REL), r.ncta);
     cl::fence_bar_init();
   }
   __syncthreads();
