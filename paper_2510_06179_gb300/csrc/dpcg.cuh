@@ -31,7 +31,7 @@ namespace dmpc {
 constexpr int kClMaxCtas = 8;     // CTAs per cluster (the portable cluster size)
 constexpr int kClThreads = 256;   // threads per CTA (the leader's team)
 constexpr int kClRows = 2;        // rows of a knot's block row per thread
-constexpr int kClNV = 2;          // widest all-reduce
+constexpr int kClNV = 3;          // widest all-reduce
 constexpr unsigned long long kClWaitNs = 4000000000ull;  // time limit of one wait (4 s)
 constexpr int ST_SYNC_TIMEOUT = 256;
 
@@ -55,6 +55,8 @@ struct ClLayout {
   int D, O, Pd, Po, A, Bm;   // float blocks
   int Pv[2], R[2], Y, Z, DL; // float vectors
   int rh, yh, zh, ph;        // halo staging, [side][NX]: side 0 = previous CTA, 1 = next CTA
+  int Lf, Wf;                // per-knot scratch of the block inversion (Cholesky factor, its inverse)
+  int pdp;                   // the previous CTA's last Phi^-1 diagonal block (NX x NX)
   int misc;                  // copy of the OCP's scalars (weights, reciprocals)
   int wpart, slots;          // all-reduce scratch: 2 x warps x kClNV, 2 x kClMaxCtas x kClNV
   int job;                   // command words written by the leader
@@ -89,6 +91,9 @@ __host__ __device__ inline ClLayout cl_layout(int nx, int nu, int kc) {
   S.yh = f; f += 2 * nx;
   S.zh = f; f += 2 * nx;
   S.ph = f; f += 2 * nx;
+  S.Lf = f; f += nx * nx * S.KB;
+  S.Wf = f; f += nx * nx * S.KB;
+  S.pdp = f; f += nx * nx;
   f = (f + 3) & ~3;
   S.misc = f; f += kMisc;
   S.wpart = f; f += 2 * (kClThreads / 32) * kClNV;
@@ -365,6 +370,190 @@ __device__ __forceinline__ float cl_step_pc(ClRun<M>& r, int rcur, int rnew, int
 // leaving WX, WU = H^T LP; halos: the next CTA's first LP (sent when push_lp, else already in
 // place), the previous CTA's last WX, WU, and both neighbours' new R (sent into the staging with
 // y = 0).  Three phases (two without push_lp).
+// a2 and a3 on the cluster: each CTA forms the Schur blocks D_k, O_k (Eq. 10, FP32, from the
+// factors A_t, B_t and the projected weights) of its own knots and of the next CTA's first knot
+// (O only), then Phi^-1: Pd_k = D_k^-1 by a Cholesky factorisation whose rows are shared by the
+// knot's threads (column by column), and Po_k = -D_k^-1 O_k D_{k-1}^-1 with the previous CTA's
+// last D^-1 read over DSMEM.  Element by element the arithmetic is that of stage_schur,
+// stage_precond and spd_inverse.  Returns whether a diagonal block of this CTA failed Cholesky
+// (its inverse is then the inverse of its diagonal, as in spd_inverse).
+template <class M>
+__device__ __noinline__ bool cl_form_blocks(ClRun<M>& r) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const int KB = r.S.KB, kl = r.kl, k = r.k0 + kl, nk = r.nk;
+  float* D = r.F(r.S.D);
+  float* O = r.F(r.S.O);
+  float* Pd = r.F(r.S.Pd);
+  float* Po = r.F(r.S.Po);
+  float* Lf = r.F(r.S.Lf);
+  float* Wf = r.F(r.S.Wf);
+  const float* A = r.F(r.S.A);
+  const float* Bm = r.F(r.S.Bm);
+  const float* mi = r.F(r.S.misc);
+  auto qproj = [&](int kk, int i) { return mi[(kk < r.T ? MS_QP : MS_QTP) + i]; };
+  auto el = [&](const float* X, int i, int j) -> const float& { return X[(i * NX + j) * KB + kl]; };
+  // D_k, O_k (rows r0, r0 + 1 of the thread's knot)
+  if (r.act) {
+    float qi[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) qi[i] = 1.f / qproj(k, i);
+    if (k == 0) {
+#pragma unroll
+      for (int q = 0; q < kClRows; ++q)
+#pragma unroll
+        for (int j = 0; j < NX; ++j) {
+          const int i = r.r0 + q;
+          D[(i * NX + j) * KB + kl] = (i == j) ? qi[i] : 0.f;
+          O[(i * NX + j) * KB + kl] = 0.f;
+        }
+    } else {
+      float qt[NX], ri[NU];
+#pragma unroll
+      for (int i = 0; i < NX; ++i) qt[i] = 1.f / qproj(k - 1, i);
+#pragma unroll
+      for (int i = 0; i < NU; ++i) ri[i] = 1.f / mi[MS_RP + i];
+#pragma unroll
+      for (int q = 0; q < kClRows; ++q) {
+        const int i = r.r0 + q;
+#pragma unroll
+        for (int j = 0; j < NX; ++j) {
+          const int hi = i > j ? i : j, lo = i > j ? j : i;   // the lower-triangle order of stage_schur
+          float sum = (hi == lo) ? qi[hi] : 0.f;
+#pragma unroll
+          for (int l = 0; l < NX; ++l) {
+            const float ah = el(A, hi, l) - (hi == l ? 1.f : 0.f), al = el(A, lo, l) - (lo == l ? 1.f : 0.f);
+            sum = fmaf(ah * qt[l], al, sum);
+          }
+#pragma unroll
+          for (int l = 0; l < NU; ++l) sum = fmaf(Bm[(hi * NU + l) * KB + kl] * ri[l], Bm[(lo * NU + l) * KB + kl], sum);
+          D[(i * NX + j) * KB + kl] = sum;
+          O[(i * NX + j) * KB + kl] = (el(A, i, j) - (i == j ? 1.f : 0.f)) * qt[j];
+        }
+      }
+    }
+  }
+  // O of the next CTA's first knot (block slot nk) from its staged A; zero without a next CTA
+  // (Po there too: the last knot's rows read block slot nk against a zero halo vector)
+  for (int e = r.tid; e < NX * NX; e += kClThreads) {
+    const int i = e / NX, j = e % NX;
+    O[e * KB + nk] = r.has_next ? (A[e * KB + nk] - (i == j ? 1.f : 0.f)) * (1.f / qproj(r.k0 + nk - 1, j)) : 0.f;
+    if (!r.has_next) Po[e * KB + nk] = 0.f;
+  }
+  __syncthreads();
+  // Pd_k = D_k^-1: Cholesky D = L L^T column by column (each thread its rows), W = L^-1 (each
+  // thread its columns), D^-1 = W^T W (each thread its rows)
+  bool fail = false;
+#pragma unroll
+  for (int j = 0; j < NX; ++j) {
+    if (r.act) {
+      float sd = el(D, j, j);
+#pragma unroll
+      for (int q = 0; q < j; ++q) sd -= el(Lf, j, q) * el(Lf, j, q);
+      if (!(sd > 0.f)) { fail = true; sd = fabsf(el(D, j, j)) + 1e-30f; }
+      const float d = sqrtf(sd);
+      const float id = 1.f / d;
+#pragma unroll
+      for (int q2 = 0; q2 < kClRows; ++q2) {
+        const int i = r.r0 + q2;
+        if (i == j) Lf[(i * NX + j) * KB + kl] = d;
+        if (i > j) {
+          float t = el(D, i, j);
+#pragma unroll
+          for (int q = 0; q < j; ++q) t -= el(Lf, i, q) * el(Lf, j, q);
+          Lf[(i * NX + j) * KB + kl] = t * id;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (r.act && !fail) {
+#pragma unroll
+    for (int q2 = 0; q2 < kClRows; ++q2) {
+      const int c = r.r0 + q2;   // this thread's columns of W
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        if (i < c) continue;
+        float t = (i == c) ? 1.f : 0.f;
+#pragma unroll
+        for (int q = 0; q < NX; ++q)
+          if (q >= c && q < i) t -= el(Lf, i, q) * el(Wf, q, c);
+        Wf[(i * NX + c) * KB + kl] = t / el(Lf, i, i);
+      }
+    }
+  }
+  __syncthreads();
+  if (r.act) {
+#pragma unroll
+    for (int q2 = 0; q2 < kClRows; ++q2) {
+      const int i = r.r0 + q2;
+#pragma unroll
+      for (int j = 0; j < NX; ++j) {
+        float v;
+        if (fail) {
+          v = (i == j) ? 1.f / (fabsf(el(D, i, i)) + 1e-30f) : 0.f;
+        } else {
+          const int hi = i > j ? i : j, lo = i > j ? j : i;
+          float sum = 0.f;
+#pragma unroll
+          for (int q = 0; q < NX; ++q)
+            if (q >= hi) sum += el(Wf, q, hi) * el(Wf, q, lo);
+          v = sum;
+        }
+        Pd[(i * NX + j) * KB + kl] = v;
+      }
+    }
+  }
+  // the previous CTA's last Pd, for this CTA's first Po
+  cl_release_barrier<M>(r);
+  if (r.has_prev && !r.broken) {
+    const uint32_t base = r.remote(r.S.Pd, r.rank - 1);
+    for (int e = r.tid; e < NX * NX; e += kClThreads)
+      r.F(r.S.pdp)[e] = cl::ld_f32(base + 4u * (uint32_t)(e * KB + r.KC - 1));
+  }
+  __syncthreads();
+  // Po_k = -Pd_k (O_k Pd_{k-1}): t1 rows into the Cholesky scratch, then Po rows
+  if (r.act && k > 0) {
+#pragma unroll
+    for (int q2 = 0; q2 < kClRows; ++q2) {
+      const int i = r.r0 + q2;
+#pragma unroll
+      for (int j = 0; j < NX; ++j) {
+        float sum = 0.f;
+#pragma unroll
+        for (int l = 0; l < NX; ++l) {
+          const float pp = (kl == 0) ? r.F(r.S.pdp)[l * NX + j] : Pd[(l * NX + j) * KB + kl - 1];
+          sum = fmaf(el(O, i, l), pp, sum);
+        }
+        Lf[(i * NX + j) * KB + kl] = sum;
+      }
+    }
+  }
+  __syncthreads();
+  if (r.act) {
+#pragma unroll
+    for (int q2 = 0; q2 < kClRows; ++q2) {
+      const int i = r.r0 + q2;
+#pragma unroll
+      for (int j = 0; j < NX; ++j) {
+        float sum = 0.f;
+        if (k > 0) {
+#pragma unroll
+          for (int l = 0; l < NX; ++l) sum = fmaf(el(Pd, i, l), el(Lf, l, j), sum);
+        }
+        Po[(i * NX + j) * KB + kl] = k > 0 ? -sum : 0.f;
+      }
+    }
+  }
+  // the next CTA's first Po (block slot nk)
+  cl_release_barrier<M>(r);
+  if (r.has_next && !r.broken) {
+    const uint32_t base = r.remote(r.S.Po, r.rank + 1);
+    for (int e = r.tid; e < NX * NX; e += kClThreads) Po[e * KB + nk] = cl::ld_f32(base + 4u * (uint32_t)(e * KB));
+  }
+  __syncthreads();
+  return __syncthreads_or(fail && r.act) != 0;
+}
+
 struct ClSync {
   int phase;
   bool broken;
@@ -466,19 +655,22 @@ struct ClResult {
   int it;
   bool converged;
   float eta0;
+  bool chol_fail;   // a diagonal Schur block failed Cholesky (formed blocks only)
 };
 
 // The distributed PCG of one OCP, run by every CTA of the cluster.  ws: the OCP's global
 // workspace (leader's layout L).  On return LP (the solution) and WX, WU (= H^T LP) are back in
 // the global workspace.
 template <class M>
-__device__ __forceinline__ ClResult cl_pcg_body(ClRun<M>& r, const KParams& P, int K, int T, float* ws);
+__device__ __forceinline__ ClResult cl_pcg_body(ClRun<M>& r, const KParams& P, int K, int T, float* ws, bool form);
 
-// Works on a register copy of the CTA's state and writes back what the solve changed.
+// Works on a register copy of the CTA's state and writes back what the solve changed.  form: the
+// S and Phi^-1 blocks are formed here from the factors (and written to the global workspace),
+// else they are read from it.
 template <class M>
-__device__ __forceinline__ ClResult cl_pcg(ClRun<M>& rin, const KParams& P, int K, int T, float* ws) {
+__device__ __forceinline__ ClResult cl_pcg(ClRun<M>& rin, const KParams& P, int K, int T, float* ws, bool form) {
   ClRun<M> r = rin;
-  const ClResult res = cl_pcg_body<M>(r, P, K, T, ws);
+  const ClResult res = cl_pcg_body<M>(r, P, K, T, ws, form);
   rin.phase = r.phase;
   rin.rel_par = r.rel_par;
   rin.broken = r.broken;
@@ -486,9 +678,9 @@ __device__ __forceinline__ ClResult cl_pcg(ClRun<M>& rin, const KParams& P, int 
 }
 
 template <class M>
-__device__ __forceinline__ ClResult cl_pcg_body(ClRun<M>& r, const KParams& P, int K, int T, float* ws) {
+__device__ __forceinline__ ClResult cl_pcg_body(ClRun<M>& r, const KParams& P, int K, int T, float* ws, bool form) {
   constexpr int NX = M::NX, NU = M::NU;
-  ClResult res{0, false, 0.f};
+  ClResult res{0, false, 0.f, false};
   r.bind(K, T);
   const Layout L = make_layout(NX, NU, K, kClThreads, P.opt.exact_hessian, 0);
   const int KP = L.KP, KB = r.S.KB, KV = r.S.KV, nk = r.nk, k0 = r.k0;
@@ -498,12 +690,12 @@ __device__ __forceinline__ ClResult cl_pcg_body(ClRun<M>& r, const KParams& P, i
   // are zero
   {
     const int nb = nk + 1;
-    const int offs[5] = {L.D, L.O, L.Pd, L.Po, L.A};
-    const int so[5] = {r.S.D, r.S.O, r.S.Pd, r.S.Po, r.S.A};
-    for (int a = 0; a < 5; ++a) {
+    const int offs[5] = {L.A, L.D, L.O, L.Pd, L.Po};
+    const int so[5] = {r.S.A, r.S.D, r.S.O, r.S.Pd, r.S.Po};
+    for (int a = 0; a < (form ? 1 : 5); ++a) {
       for (int idx = r.tid; idx < NX * NX * nb; idx += kClThreads) {
         const int e = idx / nb, j = idx % nb, k = k0 + j;
-        const bool zero_at0 = (a == 1 || a == 3 || a == 4) && k == 0;
+        const bool zero_at0 = (a == 0 || a == 2 || a == 4) && k == 0;
         r.sm[so[a] + e * KB + j] = (nk > 0 && k < K && !zero_at0) ? __ldcg(ws + offs[a] + e * KP + k) : 0.f;
       }
     }
@@ -530,6 +722,18 @@ __device__ __forceinline__ ClResult cl_pcg_body(ClRun<M>& r, const KParams& P, i
     for (int idx = r.tid; idx < 8 * NX; idx += kClThreads) r.sm[r.S.rh + idx] = 0.f;  // rh, yh, zh, ph
   }
   __syncthreads();
+  bool chol_fail = false;
+  if (form) {
+    chol_fail = cl_form_blocks<M>(r);
+    // the formed blocks of the own knots back to the global workspace (rescue, inspect)
+    const int offs[4] = {L.D, L.O, L.Pd, L.Po};
+    const int so[4] = {r.S.D, r.S.O, r.S.Pd, r.S.Po};
+    for (int a = 0; a < 4; ++a)
+      for (int idx = r.tid; idx < NX * NX * nk; idx += kClThreads) {
+        const int e = idx / nk, j = idx % nk;
+        ws[offs[a] + e * KP + k0 + j] = r.sm[so[a] + e * KB + j];
+      }
+  }
   const float tol2 = P.opt.pcg_tol * P.opt.pcg_tol;
   const float dl2 = P.opt.ru_delta * P.opt.ru_delta;
   const int maxit = P.opt.pcg_max_iters;
@@ -542,8 +746,9 @@ __device__ __forceinline__ ClResult cl_pcg_body(ClRun<M>& r, const KParams& P, i
   // true residual of the initial guess (its next-CTA LP halo came from global memory), z, eta,
   // eta_0 = gamma^T Phi^-1 gamma from the FP32-rounded gamma
   cl_true_residual<M>(r, false, rb);
-  float e0[2] = {0.f, 0.f};
+  float e0[3] = {0.f, 0.f, 0.f};
   e0[0] = cl_step_pc<M, false>(r, rb, rb, pb, 0.f);
+  if (r.tid == 0 && chol_fail) e0[2] = 1.f;
   if (r.act) {
     float gm[NX], gc[NX], gp[NX], gt[kClRows];
     const double* G = r.Dd(r.S.G);
@@ -557,10 +762,11 @@ __device__ __forceinline__ ClResult cl_pcg_body(ClRun<M>& r, const KParams& P, i
 #pragma unroll
     for (int q = 0; q < kClRows; ++q) e0[1] = fmaf(gc[r.r0 + q], gt[q], e0[1]);
   }
-  cl_sum<M, 2>(r, e0, pair_rx);
+  cl_sum<M, 3>(r, e0, pair_rx);
   float eta = e0[0];
   const float eta0 = e0[1];
   res.eta0 = eta0;
+  res.chol_fail = e0[2] > 0.f;
   float beta = 0.f;  // p = z for the first direction (the old p is zero)
   float eta_ref = eta, eta_true = eta;
   int it = 0, stall = 0;
@@ -641,11 +847,11 @@ __device__ __forceinline__ ClResult cl_pcg_body(ClRun<M>& r, const KParams& P, i
 // Leader: send a command to the other CTAs of the cluster.  The team's earlier global-memory
 // writes are released with it.
 template <class M>
-__device__ void cl_command(ClRun<M>& r, int cmd, int ocp, int K, int T) {
+__device__ void cl_command(ClRun<M>& r, int cmd, int ocp, int K, int T, int form) {
   __syncthreads();
   if (r.tid == 0) {
     int* job = reinterpret_cast<int*>(r.sm + r.S.job);
-    job[0] = cmd; job[1] = ocp; job[2] = K; job[3] = T;
+    job[0] = cmd; job[1] = ocp; job[2] = K; job[3] = T; job[4] = form;
   }
   __syncthreads();
   if (r.tid >= 1 && r.tid < (int)r.ncta && !r.broken) cl::arrive_remote(cl::map(r.bar(CB_CMD), (uint32_t)r.tid));
@@ -661,9 +867,9 @@ __device__ void cl_follower(ClRun<M>& r, const KParams& P, float* ws) {
     if (!ok) { r.broken = true; break; }
     r.cmd_par ^= 1u;
     const uint32_t jb = r.remote(r.S.job, 0);
-    const int cmd = cl::ld_s32(jb), K = cl::ld_s32(jb + 8), T = cl::ld_s32(jb + 12);
+    const int cmd = cl::ld_s32(jb), K = cl::ld_s32(jb + 8), T = cl::ld_s32(jb + 12), form = cl::ld_s32(jb + 16);
     if (cmd != CL_PCG) break;
-    cl_pcg<M>(r, P, K, T, ws);
+    cl_pcg<M>(r, P, K, T, ws, form != 0);
   }
 }
 

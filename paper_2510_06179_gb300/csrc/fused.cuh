@@ -112,6 +112,7 @@ struct Ctx {
   int df_iters;  // PCG iterations of the current solve run in the double-float rescue (inspect output)
   bool exact;  // backward with the exact Hessian of the Lagrangian (Riccati solve), else Gauss-Newton
   ClRun<M>* cl = nullptr;  // set when the OCP runs on a thread-block cluster (its PCG solves are distributed)
+  bool cl_form = false;    // the next cluster PCG forms the S and Phi^-1 blocks itself (a2, a3 skipped here)
 
   __device__ __forceinline__ float* F(int off) const { return fb + off; }
   __device__ __forceinline__ double* Dp(int off) const { return db + off; }
@@ -679,7 +680,8 @@ __device__ __noinline__ void stage_riccati_exact(Ctx<M, TEAM>& c) {
 // D_k = chi_{k-1} = A Q_{k-1}^-1 A^T + B R^-1 B^T + Q_k^-1,  O_k = phi_{k-1} = A Q_{k-1}^-1.
 // With rhs_from_qp, also gamma_spd = -(d + H G^-1 b) (App. A.2) in FP64.
 template <class M, int TEAM>
-__device__ __noinline__ void stage_schur(Ctx<M, TEAM>& c, bool rhs_from_qp) {
+// blocks = false: gamma only (the blocks are formed by the cluster PCG).
+__device__ __noinline__ void stage_schur(Ctx<M, TEAM>& c, bool rhs_from_qp, bool blocks = true) {
   constexpr int NX = M::NX, NU = M::NU;
   const KParams& P = *c.P;
   const int T = c.T, K = c.K, KP = c.KP;
@@ -697,10 +699,12 @@ __device__ __noinline__ void stage_schur(Ctx<M, TEAM>& c, bool rhs_from_qp) {
 #pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NX; ++i) qi[i] = 1.f / c.qproj(k, i);
     if (k == 0) {
+      if (blocks) {
 #pragma unroll (NX <= 8 ? 32 : 1)
-      for (int i = 0; i < NX; ++i)
+        for (int i = 0; i < NX; ++i)
 #pragma unroll (NX <= 8 ? 32 : 1)
-        for (int j = 0; j < NX; ++j) D[(i * NX + j) * KP] = (i == j) ? qi[i] : 0.f;
+          for (int j = 0; j < NX; ++j) D[(i * NX + j) * KP] = (i == j) ? qi[i] : 0.f;
+      }
       if (rhs_from_qp) {
 #pragma unroll (NX <= 8 ? 32 : 1)
         for (int i = 0; i < NX; ++i)
@@ -780,7 +784,7 @@ __device__ __noinline__ void stage_schur(Ctx<M, TEAM>& c, bool rhs_from_qp) {
 #pragma unroll (NX <= 8 ? 32 : 1)
     for (int i = 0; i < NX * NU; ++i) b[i] = Bm[i * KP + k];
 #pragma unroll (NX <= 8 ? 32 : 1)
-    for (int i = 0; i < NX; ++i) {
+    for (int i = 0; i < NX && blocks; ++i) {
 #pragma unroll (NX <= 8 ? 32 : 1)
       for (int j = 0; j <= i; ++j) {
         float s = (i == j) ? qi[i] : 0.f;
@@ -2147,14 +2151,15 @@ namespace dmpc {
 template <class M>
 __device__ __noinline__ int stage_pcg_cluster(Ctx<M, kClThreads>& c) {
   ClRun<M>& r = *c.cl;
-  cl_command<M>(r, CL_PCG, c.ocp, c.K, c.T);
-  const ClResult res = cl_pcg<M>(r, *c.P, c.K, c.T, c.fb);
+  cl_command<M>(r, CL_PCG, c.ocp, c.K, c.T, c.cl_form ? 1 : 0);
+  const ClResult res = cl_pcg<M>(r, *c.P, c.K, c.T, c.fb, c.cl_form);
   __threadfence();
   int it = res.it;
   if (r.broken) {
     c.status |= ST_SYNC_TIMEOUT;
     return it;
   }
+  if (res.chol_fail) c.status |= ST_CHOL_FAIL;
   if (!res.converged) {
     c.status |= ST_FP64_RESCUE;
     const int d = stage_pcg_df<M, kClThreads>(c, res.eta0, c.P->opt.pcg_max_iters);
@@ -2164,10 +2169,18 @@ __device__ __noinline__ int stage_pcg_cluster(Ctx<M, kClThreads>& c) {
   return it;
 }
 
+// Whether this OCP's PCG solves run on its thread-block cluster.
+template <class M, int TEAM>
+__device__ __forceinline__ bool cl_active(const Ctx<M, TEAM>& c) {
+  if constexpr (kClusterPcg && TEAM == kClThreads && M::NX % kClRows == 0 && !is_implicit<M>::value)
+    return c.cl != nullptr && !c.cl->broken;
+  return false;
+}
+
 template <class M, int TEAM>
 __device__ __forceinline__ int run_pcg(Ctx<M, TEAM>& c) {
   if constexpr (kClusterPcg && TEAM == kClThreads && M::NX % kClRows == 0 && !is_implicit<M>::value) {
-    if (c.cl && !c.cl->broken) return stage_pcg_cluster<M>(c);
+    if (cl_active(c)) return stage_pcg_cluster<M>(c);
   }
   if constexpr (M::NX <= 4) {
     if constexpr (TEAM == 32) {
@@ -2482,11 +2495,14 @@ __device__ void run_forward(Ctx<M, TEAM>& c) {
   stage_load<M, TEAM>(c, P.z_init != nullptr);
   const int iters = (P.mode == MODE_INSPECT) ? 1 : P.opt.sqp_iters;
   for (int s = 0; s < iters; ++s) {
+    const bool clf = cl_active(c);   // the cluster PCG forms the blocks (a2, a3) itself
     stage_linearise<M, TEAM>(c);
-    stage_schur<M, TEAM>(c, true);
-    stage_precond<M, TEAM>(c);
+    stage_schur<M, TEAM>(c, true, !clf);
+    if (!clf) stage_precond<M, TEAM>(c);
     copy_lam_to_lamp<M, TEAM>(c);
+    c.cl_form = clf;
     const int it = run_pcg<M, TEAM>(c);
+    c.cl_form = false;
     stage_recover<M, TEAM>(c);
     if (P.mode == MODE_INSPECT) { write_inspect<M, TEAM>(c, it); break; }
     const float a = stage_linesearch<M, TEAM>(c);
@@ -2708,22 +2724,29 @@ __device__ __noinline__ void run_backward(Ctx<M, TEAM>& c) {
     // local minimum in the exact second-order sense): this OCP gets the Gauss-Newton gradient,
     // flagged, from the linearisation already in the workspace
     c.exact = false;
-    stage_schur<M, TEAM>(c, false);
-    stage_precond<M, TEAM>(c);
+    const bool clf = cl_active(c);
+    stage_schur<M, TEAM>(c, false, !clf);
+    if (!clf) stage_precond<M, TEAM>(c);
     stage_bwd_rhs<M, TEAM>(c);
+    c.cl_form = clf;
     const int it = run_pcg<M, TEAM>(c);
+    c.cl_form = false;
     stage_bwd_finish<M, TEAM>(c, it);
     return;
   }
+  bool clf = false;
   if (P.store_mode && P.store && !is_implicit<M>::value) {  // stored records carry no A^+
     store_blocks<M, TEAM>(c, true);
   } else {
+    clf = cl_active(c);
     stage_linearise<M, TEAM>(c);
-    stage_schur<M, TEAM>(c, false);
-    stage_precond<M, TEAM>(c);
+    stage_schur<M, TEAM>(c, false, !clf);
+    if (!clf) stage_precond<M, TEAM>(c);
   }
   stage_bwd_rhs<M, TEAM>(c);
+  c.cl_form = clf;
   const int it = run_pcg<M, TEAM>(c);
+  c.cl_form = false;
   stage_bwd_finish<M, TEAM>(c, it);
 }
 
@@ -2796,7 +2819,7 @@ __global__ void __launch_bounds__(kClThreads, 1) fused_cluster_kernel(const __gr
   float* ws = P.gws + (size_t)cid * P.ws_floats;
   if (r.rank == 0) {
     for (int w = cid; w < P.n_work; w += ncl) run_one<M, kClThreads>(P, P.order[w], ws, threadIdx.x, 0, &r);
-    if (!r.broken) cl_command<M>(r, CL_EXIT, 0, 0, 0);
+    if (!r.broken) cl_command<M>(r, CL_EXIT, 0, 0, 0, 0);
   } else {
     cl_follower<M>(r, P, ws);
   }
