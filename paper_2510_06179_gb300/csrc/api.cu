@@ -236,7 +236,9 @@ static bool has_implicit_desc(const dmpc_handle* h) {
 
 // Cluster form for OCPs whose workspace does not fit in one CTA's shared memory: one cluster of
 // ncta CTAs per OCP, each holding ceil(K / ncta) knots of the PCG's blocks in shared memory.
-// cluster_ctas = 0 chooses ncta from the longest horizon (about 16 knots per CTA, at most 8 CTAs).
+// cluster_ctas = 0 chooses ncta from the longest horizon: about 40 knots per CTA (at most 8 CTAs),
+// the fewest CTAs that hold the OCP, since an iteration's cost per CTA grows slowly with its knots
+// (its chain is the two all-reduces) and fewer CTAs per OCP leave more SMs to the rest of a batch.
 // Leaves the single-team form in place when no cluster kernel fits.
 static dmpc_err configure_cluster(dmpc_handle* h, int maxK) {
   const ClusterEntry* ce = nullptr;
@@ -245,7 +247,7 @@ static dmpc_err configure_cluster(dmpc_handle* h, int maxK) {
   if (!ce) return DMPC_OK;
   const int kc_max = cl_max_kc(h->nx0);
   int ncta = h->opt.cluster_ctas;
-  if (ncta == 0) ncta = std::min(kClMaxCtas, std::max(2, (maxK + 15) / 16));
+  if (ncta == 0) ncta = std::min(kClMaxCtas, std::max(2, (maxK + 39) / 40));
   if (ncta < 2) return DMPC_OK;
   const int kc = (maxK + ncta - 1) / ncta;
   if (kc > kc_max) return DMPC_OK;

@@ -25,15 +25,19 @@ BAD = 1 | 2 | 8 | 256   # PCG cap, non-finite, bad input, cluster wait timeout
 def test_cluster_form_is_chosen_when_the_workspace_exceeds_shared_memory():
     w = workloads.rigid_body_config(B=3, T=200, seed=21, sqp_iters=1)
     b = make_batch(w)
-    assert b.get_cluster() == dict(ctas_per_cluster=8, knots_per_cta=26, clusters=3)
+    # about 40 knots per CTA: 201 knots on 6 CTAs of 34
+    assert b.get_cluster() == dict(ctas_per_cluster=6, knots_per_cta=34, clusters=3)
     assert b.get_tiling()["team_threads"] == 256
     b.close()
     b = make_batch(w, cluster_ctas=1)          # opt-out: one team per OCP from global memory
     assert b.get_cluster()["ctas_per_cluster"] == 0
     assert b.get_tiling()["smem_bytes"] == 0
     b.close()
-    b = make_batch(w, cluster_ctas=6)
-    assert b.get_cluster()["ctas_per_cluster"] == 6 and b.get_cluster()["knots_per_cta"] == 34
+    b = make_batch(w, cluster_ctas=8)
+    assert b.get_cluster()["ctas_per_cluster"] == 8 and b.get_cluster()["knots_per_cta"] == 26
+    b.close()
+    b = make_batch(w, cluster_ctas=4)          # 51 knots per CTA: more than a CTA holds
+    assert b.get_cluster()["ctas_per_cluster"] == 0
     b.close()
     short = workloads.rigid_body_config(B=2, T=24, seed=2, sqp_iters=1)
     b = make_batch(short)                      # fits in one CTA's shared memory
@@ -68,7 +72,7 @@ def test_cluster_qp_solution_matches_direct_kkt(T, seed):
 def test_cluster_forward_replay_parity():
     w = workloads.rigid_body_config(B=6, T=200, seed=21, sqp_iters=3)
     b, g = gpu_solve(w)
-    assert b.get_cluster()["ctas_per_cluster"] == 8
+    assert b.get_cluster()["ctas_per_cluster"] == 6
     assert not (g["status"] & BAD).any(), g["status"]
     res = replay_check(w, g["z"], g["alpha"])
     assert_replay_parity("cluster rigid body T=200", res, Z_GATE)
@@ -88,15 +92,15 @@ def test_every_cluster_size_matches_the_oracle(ctas):
 
 
 def test_ragged_horizons_in_one_handle_with_empty_ctas():
-    """One handle, horizons 200, 97, 40 and 6: the CTA count follows the longest horizon, so the
-    short OCPs leave trailing CTAs with no knot (T = 40: 41 knots as 6 per CTA, CTA 7 empty;
-    T = 6: one knot per CTA)."""
+    """One handle, horizons 200, 97, 40 and 6 on clusters of 8 CTAs (the count follows the longest
+    horizon), so the short OCPs leave trailing CTAs with no knot (T = 40: 41 knots as 6 per CTA,
+    CTA 7 empty; T = 6: one knot per CTA)."""
     import torch
     from paper_2510_06179_gb300.solver import OCPBatch
     ensure_built()
     items = [workloads.rigid_body_config(B=1, T=T, seed=30 + T, sqp_iters=2) for T in (200, 97, 40, 6)]
     descs = [(w.model, w.nx, w.nu, w.T, w.dt) for w in items]
-    b = OCPBatch(descs, device="cuda:0", sqp_iters=2, line_search=1, pcg_tol=1e-9)
+    b = OCPBatch(descs, device="cuda:0", sqp_iters=2, line_search=1, pcg_tol=1e-9, cluster_ctas=8)
     assert b.get_cluster()["ctas_per_cluster"] == 8
     cat = lambda f: np.concatenate([getattr(w, f).ravel() for w in items])
     out = b.solve(dev(cat("x_s")), dev(cat("theta")), dev(cat("x_ref")))
