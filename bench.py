@@ -46,10 +46,11 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=256, help="OCPs in the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement of the JSON line")
-    ap.add_argument("--profile-case", choices=["cartpole", "vehicle"], default=None,
+    ap.add_argument("--profile-case", choices=["cartpole", "vehicle", "rigid_body"], default=None,
                     help="run a small untimed case for a profiler and exit: the bench batch (three warm-up "
-                         "forward launches, then one forward and one backward launch), or a one-wave vehicle "
-                         "batch (152 OCPs, T 100; three warm-up forward launches, then one)")
+                         "forward launches, then one forward and one backward launch), a one-wave vehicle "
+                         "batch (152 OCPs, T 100; three warm-up forward launches, then one), or one rigid-body "
+                         "OCP (T 256, 2 SQP iterations, thread-block cluster form; one warm-up launch, then one)")
     ap.add_argument("--suite", default=None, help="also run the comparison suite and write it to this JSON file")
     ap.add_argument("--suite-only", action="store_true", help="run only the comparison suite")
     return ap.parse_args()
@@ -294,19 +295,23 @@ def profile_case(name):
         w = workload(0)
         b = OCPBatch(("cartpole", 4, 1, T, 0.05), batch=B, device=dev, sqp_iters=SQP_ITERS, line_search=1,
                      pcg_tol=PCG_TOL, warm_start=0)
-    else:
+    elif name == "vehicle":
         w = workloads.vehicle_config(B=152, T=100, seed=0, sqp_iters=SQP_ITERS)
         b = OCPBatch(("single_track", 6, 2, 100, 0.02), batch=152, device=dev, sqp_iters=SQP_ITERS, line_search=1,
                      pcg_tol=PCG_TOL, warm_start=0)
+    else:   # one 12-state rigid-body OCP, T 256, 2 SQP iterations: the thread-block cluster form
+        w = workloads.rigid_body_config(B=1, T=256, seed=3, sqp_iters=2)
+        b = OCPBatch(("rigid_body12", 12, 4, 256, w.dt), batch=1, device=dev, sqp_iters=2, line_search=1,
+                     pcg_tol=PCG_TOL, warm_start=0)
     inp = (t(w.x_s), t(w.theta), t(w.x_ref))
-    for _ in range(4):
+    for _ in range(4 if name != "rigid_body" else 2):
         b.solve(*inp, want_stats=False)
     if name == "cartpole":
         dl = torch.zeros(w.B * w.n, device=dev)
         dl.view(w.B, -1)[:, 4] = 1.0
         b.vjp(dl, want_stats=False)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": name, "tiling": b.get_tiling()}))
+    print(json.dumps({"profile_case": name, "tiling": b.get_tiling(), "cluster": b.get_cluster()}))
     b.close()
 
 
