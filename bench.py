@@ -113,8 +113,8 @@ def _code_tokens(text):
 # the translation unit of the benchmarked kernel (fused_kernel<32, CartPole>) and every header
 # it includes: the code the traffic capture describes; host-side sources (the C ABI, tiling
 # rules, other models' units) do not change that kernel
-KERNEL_UNIT = ("k_cartpole.cu", "launch_impl.cuh", "launch.h", "fused.cuh", "plain.cuh", "device_util.cuh",
-               "dfloat.cuh", "models.cuh", "params.h")
+KERNEL_UNIT = ("k_cartpole.cu", "launch_impl.cuh", "launch.h", "fused.cuh", "dpcg.cuh", "cluster.cuh", "plain.cuh",
+               "device_util.cuh", "dfloat.cuh", "models.cuh", "params.h")
 
 
 def kernel_source_hash():

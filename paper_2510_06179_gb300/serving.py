@@ -65,9 +65,17 @@ class SlotClass:
         self.lib = self.batch.lib
         _lib.check(self.lib.dmpc_set_stream(self.batch.h, ctypes.c_void_p(self.stream.cuda_stream)), self.batch.h)
         b = self.batch
-        self.x_s = torch.zeros(b.n_xs, device=device)
-        self.theta = torch.zeros(b.n_th, device=device)
-        self.x_ref = torch.zeros(b.n_xref, device=device)
+        # the three input arrays are views of one buffer, so an admission is one scatter
+        self.inputs = torch.zeros(b.n_xs + b.n_th + b.n_xref, device=device)
+        self.x_s = self.inputs[:b.n_xs]
+        self.theta = self.inputs[b.n_xs:b.n_xs + b.n_th]
+        self.x_ref = self.inputs[b.n_xs + b.n_th:]
+        self.in_base = (0, b.n_xs, b.n_xs + b.n_th)
+        # pinned staging of admitted values and their positions, two buffers used in turn (a
+        # buffer is refilled only after the copy out of it has run)
+        self.stage = [None, None]
+        self.stage_ev = [None, None]
+        self.stage_i = 0
         self.z = torch.zeros(b.n_z, device=device)
         self.lam = torch.zeros(b.n_lam, device=device)
         self.status = torch.zeros(slots, dtype=torch.int32, device=device)
@@ -82,8 +90,20 @@ class SlotClass:
         self.device = device
 
     def tensor_bytes(self):
-        return sum(t.numel() * t.element_size() for t in (self.x_s, self.theta, self.x_ref, self.z, self.lam,
-                                                           self.status, self.idx_d))
+        return sum(t.numel() * t.element_size() for t in (self.inputs, self.z, self.lam, self.status, self.idx_d))
+
+    def _staging(self, n):
+        """The next pinned staging buffer pair (values, positions) with room for n entries."""
+        k = self.stage_i
+        self.stage_i ^= 1
+        if self.stage_ev[k] is not None:
+            self.stage_ev[k].synchronize()
+        st = self.stage[k]
+        if st is None or st[0].numel() < n:
+            m = max(n, 2 * st[0].numel() if st is not None else 4096)
+            st = (torch.empty(m, dtype=torch.float32).pin_memory(), torch.empty(m, dtype=torch.int64).pin_memory())
+            self.stage[k] = st
+        return k, st
 
     def idle(self):
         return self.inflight is None or self.inflight[0].query()
@@ -104,16 +124,27 @@ class SlotClass:
         for i, (s, r) in enumerate(new):
             descs[i] = _lib.dmpc_ocp_desc(MODEL_IDS[r.model], r.nx, r.nu, r.T, r.dt)
         reset = np.ones(len(new), dtype=np.int32)
+        # values of all admitted requests and their positions in the input buffer: one copy of
+        # each out of the pinned staging, one scatter
+        total = sum(r.x_s.size + r.theta.size + r.x_ref.size for _, r in new)
+        k, (sv, sp) = self._staging(total)
+        vals, pos = sv.numpy(), sp.numpy()
+        o = 0
+        for s, r in new:
+            for base, off, a in ((self.in_base[0], b.xs_off, r.x_s), (self.in_base[1], b.th_off, r.theta),
+                                 (self.in_base[2], b.xref_off, r.x_ref)):
+                m = a.size
+                vals[o:o + m] = a.reshape(-1)
+                start = base + int(off[s])
+                pos[o:o + m] = np.arange(start, start + m, dtype=np.int64)
+                o += m
         with torch.cuda.stream(self.stream):
-            # values of all admitted requests and their arena positions, one scatter per array
-            for arena, off, field in ((self.x_s, b.xs_off, "x_s"), (self.theta, b.th_off, "theta"),
-                                      (self.x_ref, b.xref_off, "x_ref")):
-                vals = np.concatenate([getattr(r, field).reshape(-1) for _, r in new]).astype(np.float32)
-                pos = np.concatenate([np.arange(off[s], off[s] + getattr(r, field).size, dtype=np.int64)
-                                      for s, r in new])
-                v_d = torch.from_numpy(vals).pin_memory().to(self.device, non_blocking=True)
-                p_d = torch.from_numpy(pos).pin_memory().to(self.device, non_blocking=True)
-                arena.index_copy_(0, p_d, v_d)
+            v_d = sv[:total].to(self.device, non_blocking=True)
+            p_d = sp[:total].to(self.device, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+            self.stage_ev[k] = ev
+            self.inputs.index_copy_(0, p_d, v_d)
             _lib.check(self.lib.dmpc_set_ocps(b.h, len(new), idx.ctypes.data_as(ctypes.c_void_p),
                                               descs, reset.ctypes.data_as(ctypes.c_void_p)), b.h)
         return len(new)
@@ -270,9 +301,12 @@ class ServingEngine:
                     if not c.idle():
                         active = True
                         continue
-                    n_done += c.retire(start_ev, keep_solutions)
-                    c.admit()
-                    active = c.advance(self.plain, record_alpha=keep_solutions) or active
+                    if c.inflight is not None:
+                        n_done += c.retire(start_ev, keep_solutions)
+                    if c.queue and c.free:
+                        c.admit()
+                    if c.busy:
+                        active = c.advance(self.plain, record_alpha=keep_solutions) or active
                 if self.queues[key] and not any(c.free for c in arenas):
                     c = self._grow(key)        # every slot taken and requests waiting
                     if c is not None:
