@@ -56,6 +56,10 @@ struct ClLayout {
   int Pv[2], R[2], Y, Z, DL; // float vectors
   int rh, yh, zh, ph;        // halo staging, [side][NX]: side 0 = previous CTA, 1 = next CTA
   int Lf, Wf;                // per-knot scratch of the block inversion (Cholesky factor, its inverse)
+  // double-float rescue (aliases the inversion scratch): vectors X, R, P, Y, Z, WX, WU (one hi/lo
+  // float pair per element, element i of vector slot j at 2 (i KV + j)) and halo staging
+  // [side][NX] pairs for r, y, z, p
+  int dX, dR, dP, dY, dZ, dWX, dWU, drh, dyh, dzh, dph;
   int pdp;                   // the previous CTA's last Phi^-1 diagonal block (NX x NX)
   int misc;                  // copy of the OCP's scalars (weights, reciprocals)
   int wpart, slots;          // all-reduce scratch: 2 x warps x kClNV, 2 x kClMaxCtas x kClNV
@@ -91,8 +95,24 @@ __host__ __device__ inline ClLayout cl_layout(int nx, int nu, int kc) {
   S.yh = f; f += 2 * nx;
   S.zh = f; f += 2 * nx;
   S.ph = f; f += 2 * nx;
-  S.Lf = f; f += nx * nx * S.KB;
-  S.Wf = f; f += nx * nx * S.KB;
+  S.Lf = f;
+  S.Wf = f + nx * nx * S.KB;
+  {
+    int g = f;
+    const int dv = 2 * nx * S.KV;
+    S.dX = g; g += dv;
+    S.dR = g; g += dv;
+    S.dP = g; g += dv;
+    S.dY = g; g += dv;
+    S.dZ = g; g += dv;
+    S.dWX = g; g += dv;
+    S.dWU = g; g += 2 * nu * S.KV;
+    S.drh = g; g += 4 * nx;
+    S.dyh = g; g += 4 * nx;
+    S.dzh = g; g += 4 * nx;
+    S.dph = g; g += 4 * nx;
+    f = (g > f + 2 * nx * nx * S.KB) ? g : f + 2 * nx * nx * S.KB;
+  }
   S.pdp = f; f += nx * nx;
   f = (f + 3) & ~3;
   S.misc = f; f += kMisc;
@@ -651,37 +671,377 @@ __device__ __forceinline__ void cl_true_residual(ClRun<M>& r, bool push_lp, int 
   r.broken = st.broken;
 }
 
+// ---- double-float rescue on the cluster (stage_pcg_df distributed) ------------------------
+
+// Sum a double-float value over the cluster: warp butterflies and warp partials with df_add,
+// then every CTA's partial into a slot of every CTA (st.async of its two floats), summed in rank
+// order; bitwise the same total everywhere.  halo_rx as in cl_sum.
+template <class M>
+__device__ __forceinline__ dfl cl_sum_df(ClRun<M>& r, dfl v, uint32_t halo_rx) {
+  v = df_warp_sum(v);
+  const int b = r.phase & 1;
+  const uint32_t par = (uint32_t)(r.phase >> 1) & 1u;
+  float* wp = r.F(r.S.wpart) + b * (kClThreads / 32) * kClNV;
+  float* sl = r.F(r.S.slots) + b * kClMaxCtas * kClNV;
+  if ((r.tid & 31) == 0) { wp[(r.tid >> 5) * kClNV] = v.hi; wp[(r.tid >> 5) * kClNV + 1] = v.lo; }
+  __syncthreads();
+  if (r.tid < (int)r.ncta && !r.broken) {
+    dfl t = {wp[0], wp[1]};
+    for (int q = 1; q < kClThreads / 32; ++q) t = df_add(t, dfl{wp[q * kClNV], wp[q * kClNV + 1]});
+    const uint32_t dst = r.remote(r.S.slots + b * kClMaxCtas * kClNV + (int)r.rank * kClNV, (uint32_t)r.tid);
+    const uint32_t rb = r.red_bar((uint32_t)r.tid);
+    cl::st_async_f32(dst, t.hi, rb);
+    cl::st_async_f32(dst + 4u, t.lo, rb);
+  }
+  if (r.tid == 0 && !r.broken) cl::arrive_expect_tx(r.bar(b), r.ncta * 8u + halo_rx);
+  bool ok = r.broken ? false : cl::wait(r.bar(b), par, kClWaitNs);
+  ok = __syncthreads_and(ok) != 0;
+  if (!ok) r.broken = true;
+  dfl t = {sl[0], sl[1]};
+  for (uint32_t q = 1; q < r.ncta; ++q) t = df_add(t, dfl{sl[q * kClNV], sl[q * kClNV + 1]});
+  ++r.phase;
+  return t;
+}
+
+// Send this thread's rows of a boundary knot's double-float values (a, b) into the df staging
+// arrays of the neighbours (side 1 of the previous CTA, side 0 of the next) for the coming phase.
+template <class M>
+__device__ __forceinline__ void cl_push_df(ClRun<M>& r, int st_a, int st_b, const dfl* a, const dfl* b) {
+  constexpr int NX = M::NX;
+  if (!r.act || r.broken) return;
+  auto send = [&](uint32_t q, int side) {
+    const uint32_t rb = r.red_bar(q);
+    const uint32_t da = r.remote(st_a + 2 * (side * NX + r.r0), q), db = r.remote(st_b + 2 * (side * NX + r.r0), q);
+#pragma unroll
+    for (int i = 0; i < kClRows; ++i) {
+      cl::st_async_f32(da + 8u * i, a[i].hi, rb);
+      cl::st_async_f32(da + 8u * i + 4u, a[i].lo, rb);
+      cl::st_async_f32(db + 8u * i, b[i].hi, rb);
+      cl::st_async_f32(db + 8u * i + 4u, b[i].lo, rb);
+    }
+  };
+  if (r.kl == 0 && r.has_prev) send(r.rank - 1, 1);
+  if (r.kl == r.nk - 1 && r.has_next) send(r.rank + 1, 0);
+}
+
+// halo slots of the df vector `v` (slot 0 from side 0, slot nk + 1 from side 1) = a + s b from
+// the df staging
+template <class M>
+__device__ __forceinline__ void cl_halo_df(ClRun<M>& r, dfl* v, int st_a, int st_b, dfl sc) {
+  constexpr int NX = M::NX;
+  if (r.tid < 2 * NX) {
+    const int side = r.tid / NX, i = r.tid % NX;
+    if (side == 0 ? r.has_prev : r.has_next) {
+      const dfl* ha = reinterpret_cast<const dfl*>(r.F(st_a));
+      const dfl* hb = reinterpret_cast<const dfl*>(r.F(st_b));
+      v[i * r.S.KV + (side == 0 ? 0 : r.nk + 1)] = df_add(ha[side * NX + i], df_mul(sc, hb[side * NX + i]));
+    }
+  }
+  __syncthreads();
+}
+
+// out = S v (= H G^-1 H^T v) on the own knots in double-float from the FP32 factors and the
+// reciprocal weights (df_apply distributed): v needs its next-CTA halo slot; one phase inside
+// (the previous CTA's last H^T v).
+template <class M>
+__device__ __forceinline__ void cl_df_apply(ClRun<M>& r, const dfl* v, dfl* out, const dfl (&qx)[M::NX],
+                                            const dfl (&qT)[M::NX], const dfl (&ri)[M::NU]) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const int KB = r.S.KB, KV = r.S.KV, kl = r.kl, sl = kl + 1, k = r.k0 + kl;
+  const float* A = r.F(r.S.A);
+  const float* Bm = r.F(r.S.Bm);
+  dfl* WX = reinterpret_cast<dfl*>(r.F(r.S.dWX));
+  dfl* WU = reinterpret_cast<dfl*>(r.F(r.S.dWU));
+  if (r.act) {
+    const bool send = kl == r.nk - 1 && r.has_next && !r.broken;
+    const uint32_t q = r.rank + 1, rbar = send ? r.red_bar(q) : 0u;
+#pragma unroll
+    for (int j = 0; j < kClRows; ++j) {
+      const int i = r.r0 + j;
+      dacc a = dacc_zero();
+      dacc_add(a, v[i * KV + sl]);
+      if (k < r.T) {   // (A_k + I)^T v_{k+1} - v_{k+1}
+#pragma unroll
+        for (int c = 0; c < NX; ++c) dacc_fma(a, A[(c * NX + i) * KB + kl + 1], v[c * KV + sl + 1]);
+        dacc_add(a, df_neg(v[i * KV + sl + 1]));
+      }
+      const dfl w = dacc_get(a);
+      WX[i * KV + sl] = w;
+      if (send) {
+        const uint32_t d = r.remote(r.S.dWX + 2 * (i * KV + 0), q);
+        cl::st_async_f32(d, w.hi, rbar);
+        cl::st_async_f32(d + 4u, w.lo, rbar);
+      }
+    }
+    for (int u = r.r0 / kClRows; u < NU; u += r.RG) {
+      dacc a = dacc_zero();
+      if (k < r.T) {
+#pragma unroll
+        for (int c = 0; c < NX; ++c) dacc_fma(a, Bm[(c * NU + u) * KB + kl + 1], v[c * KV + sl + 1]);
+      }
+      const dfl w = dacc_get(a);
+      WU[u * KV + sl] = w;
+      if (send) {
+        const uint32_t d = r.remote(r.S.dWU + 2 * (u * KV + 0), q);
+        cl::st_async_f32(d, w.hi, rbar);
+        cl::st_async_f32(d + 4u, w.lo, rbar);
+      }
+    }
+  }
+  cl_barrier<M>(r, r.has_prev ? 8u * (NX + NU) : 0u);
+  if (r.act) {
+    dfl vx[NX], vu[NU];
+    if (k > 0) {
+#pragma unroll
+      for (int j = 0; j < NX; ++j) vx[j] = df_mul(WX[j * KV + sl - 1], qx[j]);   // k - 1 < T
+#pragma unroll
+      for (int j = 0; j < NU; ++j) vu[j] = df_mul(WU[j * KV + sl - 1], ri[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < kClRows; ++j) {
+      const int i = r.r0 + j;
+      dacc a = dacc_zero();
+      dacc_add(a, df_mul(WX[i * KV + sl], k < r.T ? qx[i] : qT[i]));
+      if (k > 0) {
+#pragma unroll
+        for (int c = 0; c < NX; ++c) dacc_fma(a, A[(i * NX + c) * KB + kl], vx[c]);
+        dacc_add(a, df_neg(vx[i]));
+#pragma unroll
+        for (int c = 0; c < NU; ++c) dacc_fma(a, Bm[(i * NU + c) * KB + kl], vu[c]);
+      }
+      out[i * KV + sl] = dacc_get(a);
+    }
+  }
+}
+
+// Rows of z = Phi^-1 v in double-float (FP32 blocks, compensated accumulation); v needs both halo
+// slots.
+template <class M>
+__device__ __forceinline__ void cl_precond_df(const ClRun<M>& r, const dfl* v, dfl (&z)[kClRows]) {
+  constexpr int NX = M::NX;
+  const int KB = r.S.KB, KV = r.S.KV, kl = r.kl, sl = kl + 1;
+  const float* Pd = r.F(r.S.Pd);
+  const float* Po = r.F(r.S.Po);
+#pragma unroll
+  for (int q = 0; q < kClRows; ++q) {
+    const int i = r.r0 + q;
+    dacc a = dacc_zero();
+#pragma unroll
+    for (int j = 0; j < NX; ++j) dacc_fma(a, Pd[(i * NX + j) * KB + kl], v[j * KV + sl]);
+#pragma unroll
+    for (int j = 0; j < NX; ++j) dacc_fma(a, Po[(i * NX + j) * KB + kl], v[j * KV + sl - 1]);
+#pragma unroll
+    for (int j = 0; j < NX; ++j) dacc_fma(a, Po[(j * NX + i) * KB + kl + 1], v[j * KV + sl + 1]);
+    z[q] = dacc_get(a);
+  }
+}
+
+struct ClDfOut {
+  int phase, it;
+  bool broken, converged, breakdown;
+};
+
+// The double-float rescue of one solve on the cluster (stage_pcg_df's iteration with every
+// vector in shared memory): continues from the FP64 solution LP; on return LP holds the result
+// (the caller then forms the FP64 true residual and H^T LP).  Three phases per iteration (the
+// operator's halo, p^T S p with the r, S p halos, r^T z with the z, p halos).
+template <class M>
+__device__ __noinline__ ClDfOut cl_pcg_df(ClRun<M> r, float eta0f, int maxit, float tol) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const int KV = r.S.KV, sl = r.kl + 1;
+  ClDfOut out{0, 0, false, false, false};
+  dfl* X = reinterpret_cast<dfl*>(r.F(r.S.dX));
+  dfl* R = reinterpret_cast<dfl*>(r.F(r.S.dR));
+  dfl* Pv = reinterpret_cast<dfl*>(r.F(r.S.dP));
+  dfl* Y = reinterpret_cast<dfl*>(r.F(r.S.dY));
+  dfl* Z = reinterpret_cast<dfl*>(r.F(r.S.dZ));
+  double* LP = r.Dd(r.S.LP);
+  const double* G = r.Dd(r.S.G);
+  dfl qx[NX], qT[NX], ri[NU];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) { qx[i] = df_from(r.qinv(0, i)); qT[i] = df_from(r.qinv(r.T, i)); }
+#pragma unroll
+  for (int i = 0; i < NU; ++i) ri[i] = df_from(r.rinv(i));
+  const dfl thr = df_mulf(df_make(eta0f), tol * tol);
+  const dfl zero = {0.f, 0.f};
+  const uint32_t pair_rx = r.halo_bytes(16u * NX);   // two df vectors of NX from each neighbour
+  for (int idx = r.tid; idx < NX * KV; idx += kClThreads) {
+    X[idx] = zero; R[idx] = zero; Pv[idx] = zero; Y[idx] = zero; Z[idx] = zero;
+  }
+  for (int idx = r.tid; idx < 16 * NX; idx += kClThreads) r.sm[r.S.drh + idx] = 0.f;   // the four stagings
+  __syncthreads();
+  dfl xr[kClRows];
+  if (r.act) {
+#pragma unroll
+    for (int q = 0; q < kClRows; ++q) { xr[q] = df_from(LP[(r.r0 + q) * KV + sl]); X[(r.r0 + q) * KV + sl] = xr[q]; }
+  }
+  // X's next-CTA halo (the previous CTA receives this CTA's first knot), then R = gamma - S X
+  cl_push_df<M>(r, r.S.dzh, r.S.dph, xr, xr);
+  cl_barrier<M>(r, r.halo_bytes(16u * NX));
+  cl_halo_df<M>(r, X, r.S.dzh, r.S.dzh, zero);
+  cl_df_apply<M>(r, X, Y, qx, qT, ri);
+  dfl rr[kClRows], zr[kClRows];
+  if (r.act) {
+#pragma unroll
+    for (int q = 0; q < kClRows; ++q) {
+      const int i = r.r0 + q;
+      rr[q] = df_sub(df_from(G[i * KV + sl]), Y[i * KV + sl]);
+      R[i * KV + sl] = rr[q];
+    }
+  }
+  cl_push_df<M>(r, r.S.drh, r.S.dyh, rr, rr);
+  cl_barrier<M>(r, pair_rx);
+  cl_halo_df<M>(r, R, r.S.drh, r.S.drh, zero);
+  // z = Phi^-1 r, p = z, eta = r^T z
+  dacc ea = dacc_zero();
+  if (r.act) {
+    cl_precond_df<M>(r, R, zr);
+#pragma unroll
+    for (int q = 0; q < kClRows; ++q) {
+      const int i = r.r0 + q;
+      Z[i * KV + sl] = zr[q];
+      Pv[i * KV + sl] = zr[q];
+      dacc_fma(ea, rr[q], zr[q]);
+    }
+  }
+  cl_push_df<M>(r, r.S.dzh, r.S.dph, zr, zr);
+  dfl eta = cl_sum_df<M>(r, dacc_get(ea), pair_rx);
+  cl_halo_df<M>(r, Pv, r.S.dzh, r.S.dzh, zero);
+  int it = 0;
+  bool converged = !(eta.hi > thr.hi);
+  while (!converged && it < maxit && !r.broken) {
+    // y = S p, v = p^T y; boundary knots send r and y
+    cl_df_apply<M>(r, Pv, Y, qx, qT, ri);
+    dacc va = dacc_zero();
+    dfl yr[kClRows], pr[kClRows];
+    if (r.act) {
+#pragma unroll
+      for (int q = 0; q < kClRows; ++q) {
+        const int i = r.r0 + q;
+        yr[q] = Y[i * KV + sl];
+        rr[q] = R[i * KV + sl];
+        pr[q] = Pv[i * KV + sl];
+        dacc_fma(va, pr[q], yr[q]);
+      }
+    }
+    cl_push_df<M>(r, r.S.drh, r.S.dyh, rr, yr);
+    const dfl v = cl_sum_df<M>(r, dacc_get(va), pair_rx);
+    if (!(v.hi > 0.f) || !isfinite(v.hi)) { out.breakdown = true; break; }
+    const dfl alpha = df_div(eta, v);
+    // x += alpha p, r -= alpha y; r's halos from the neighbours' old r and y
+    if (r.act) {
+#pragma unroll
+      for (int q = 0; q < kClRows; ++q) {
+        const int i = r.r0 + q;
+        X[i * KV + sl] = df_add(X[i * KV + sl], df_mul(alpha, pr[q]));
+        rr[q] = df_sub(rr[q], df_mul(alpha, yr[q]));
+        R[i * KV + sl] = rr[q];
+      }
+    }
+    cl_halo_df<M>(r, R, r.S.drh, r.S.dyh, df_neg(alpha));
+    // z = Phi^-1 r, eta = r^T z; boundary knots send z and the old p
+    dacc na = dacc_zero();
+    if (r.act) {
+      cl_precond_df<M>(r, R, zr);
+#pragma unroll
+      for (int q = 0; q < kClRows; ++q) {
+        Z[(r.r0 + q) * KV + sl] = zr[q];
+        dacc_fma(na, rr[q], zr[q]);
+      }
+    }
+    cl_push_df<M>(r, r.S.dzh, r.S.dph, zr, pr);
+    const dfl eta_new = cl_sum_df<M>(r, dacc_get(na), pair_rx);
+    ++it;
+    if (!(eta_new.hi > thr.hi)) { converged = true; break; }
+    if (!isfinite(eta_new.hi)) break;
+    const dfl beta = df_div(eta_new, eta);
+    eta = eta_new;
+    // p = z + beta p (own rows and the next CTA's halo from its z and old p)
+    if (r.act) {
+#pragma unroll
+      for (int q = 0; q < kClRows; ++q) {
+        const int i = r.r0 + q;
+        Pv[i * KV + sl] = df_add(zr[q], df_mul(beta, pr[q]));
+      }
+    }
+    cl_halo_df<M>(r, Pv, r.S.dzh, r.S.dph, beta);
+  }
+  if (r.act) {
+#pragma unroll
+    for (int q = 0; q < kClRows; ++q) LP[(r.r0 + q) * KV + sl] = df_to(X[(r.r0 + q) * KV + sl]);
+  }
+  out.phase = r.phase;
+  out.broken = r.broken;
+  out.it = it;
+  out.converged = converged;
+  return out;
+}
+
 struct ClResult {
   int it;
   bool converged;
   float eta0;
   bool chol_fail;   // a diagonal Schur block failed Cholesky (formed blocks only)
+  int df_it;        // iterations of the double-float rescue (0 when FP32 converged)
+  bool df_breakdown;
+  bool df_converged;
 };
 
 // The distributed PCG of one OCP, run by every CTA of the cluster.  ws: the OCP's global
 // workspace (leader's layout L).  On return LP (the solution) and WX, WU (= H^T LP) are back in
 // the global workspace.
-template <class M>
-__device__ __forceinline__ ClResult cl_pcg_body(ClRun<M>& r, const KParams& P, int K, int T, float* ws, bool form);
+// State of a CTA after a stage of the solve: the all-reduce counters and the result so far.
+struct ClStage {
+  int phase;
+  uint32_t rel_par;
+  bool broken;
+  int rb;
+  ClResult res;
+};
 
-// Works on a register copy of the CTA's state and writes back what the solve changed.  form: the
-// S and Phi^-1 blocks are formed here from the factors (and written to the global workspace),
-// else they are read from it.
+template <class M>
+__device__ __noinline__ ClStage cl_pcg_fp32(ClRun<M> r, const KParams& P, float* ws, bool form);
+template <class M>
+__device__ __noinline__ ClStage cl_pcg_finish(ClRun<M> r, const KParams& P, float* ws, ClStage st);
+
+// One solve on the cluster, in stages that each take the CTA's state by value (so every stage
+// keeps it in registers): the FP32 iteration, the double-float rescue when that stagnated, and the
+// write-back.  form: the S and Phi^-1 blocks are formed here from the factors (and written to the
+// global workspace), else they are read from it.
 template <class M>
 __device__ __forceinline__ ClResult cl_pcg(ClRun<M>& rin, const KParams& P, int K, int T, float* ws, bool form) {
-  ClRun<M> r = rin;
-  const ClResult res = cl_pcg_body<M>(r, P, K, T, ws, form);
-  rin.phase = r.phase;
-  rin.rel_par = r.rel_par;
-  rin.broken = r.broken;
-  return res;
+  rin.bind(K, T);
+  ClStage st = cl_pcg_fp32<M>(rin, P, ws, form);
+  rin.phase = st.phase;
+  rin.rel_par = st.rel_par;
+  rin.broken = st.broken;
+  if (!st.res.converged && !rin.broken) {
+    const ClDfOut d = cl_pcg_df<M>(rin, st.res.eta0, P.opt.pcg_max_iters, P.opt.pcg_tol);
+    rin.phase = d.phase;
+    rin.broken = d.broken;
+    st.res.df_it = d.it;
+    st.res.df_breakdown = d.breakdown;
+    st.res.df_converged = d.converged;
+    if (!rin.broken) {
+      const ClSync sy = cl_hp_residual<M>(rin, true, st.rb);
+      rin.phase = sy.phase;
+      rin.broken = sy.broken;
+    }
+  }
+  st.phase = rin.phase;
+  st.broken = rin.broken;
+  st = cl_pcg_finish<M>(rin, P, ws, st);
+  rin.phase = st.phase;
+  rin.rel_par = st.rel_par;
+  rin.broken = st.broken;
+  return st.res;
 }
 
 template <class M>
-__device__ __forceinline__ ClResult cl_pcg_body(ClRun<M>& r, const KParams& P, int K, int T, float* ws, bool form) {
+__device__ __noinline__ ClStage cl_pcg_fp32(ClRun<M> r, const KParams& P, float* ws, bool form) {
   constexpr int NX = M::NX, NU = M::NU;
-  ClResult res{0, false, 0.f, false};
-  r.bind(K, T);
+  const int K = r.K;
+  ClResult res{0, false, 0.f, false, 0, false, false};
   const Layout L = make_layout(NX, NU, K, kClThreads, P.opt.exact_hessian, 0);
   const int KP = L.KP, KB = r.S.KB, KV = r.S.KV, nk = r.nk, k0 = r.k0;
   const double* wd = reinterpret_cast<const double*>(ws);
@@ -825,6 +1185,21 @@ __device__ __forceinline__ ClResult cl_pcg_body(ClRun<M>& r, const KParams& P, i
     }
     cl_true_residual<M>(r, true, rb);
   }
+  res.it = it;
+  res.converged = converged && !r.broken;
+  return ClStage{r.phase, r.rel_par, r.broken, rb, res};
+}
+
+// Own knots of LP, WX, WU back to the global workspace, then a release barrier over the cluster.
+template <class M>
+__device__ __noinline__ ClStage cl_pcg_finish(ClRun<M> r, const KParams& P, float* ws, ClStage st) {
+  constexpr int NX = M::NX, NU = M::NU;
+  r.phase = st.phase;
+  r.rel_par = st.rel_par;
+  r.broken = st.broken;
+  const Layout L = make_layout(NX, NU, r.K, kClThreads, P.opt.exact_hessian, 0);
+  const int KP = L.KP, KV = r.S.KV, nk = r.nk, k0 = r.k0;
+  double* LP = r.Dd(r.S.LP);
   // own knots of LP, WX, WU back to the global workspace
   if (!r.broken) {
     double* gd = reinterpret_cast<double*>(ws);
@@ -839,9 +1214,10 @@ __device__ __forceinline__ ClResult cl_pcg_body(ClRun<M>& r, const KParams& P, i
     }
   }
   cl_release_barrier<M>(r);
-  res.it = it;
-  res.converged = converged && !r.broken;
-  return res;
+  st.phase = r.phase;
+  st.rel_par = r.rel_par;
+  st.broken = r.broken;
+  return st;
 }
 
 // Leader: send a command to the other CTAs of the cluster.  The team's earlier global-memory

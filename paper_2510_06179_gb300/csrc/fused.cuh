@@ -2146,8 +2146,8 @@ __device__ __noinline__ int stage_pcg_warp_cg(Ctx<M, 32>& c) {
 #include "dpcg.cuh"
 namespace dmpc {
 
-// Leader side of the distributed PCG: hand the solve to every CTA of the cluster, take part in
-// it, and finish a stagnated solve with the double-float rescue from the global workspace.
+// Leader side of the distributed PCG: hand the solve to every CTA of the cluster and take part in
+// it (a stagnated solve is finished by the cluster's double-float rescue).
 template <class M>
 __device__ __noinline__ int stage_pcg_cluster(Ctx<M, kClThreads>& c) {
   ClRun<M>& r = *c.cl;
@@ -2160,11 +2160,12 @@ __device__ __noinline__ int stage_pcg_cluster(Ctx<M, kClThreads>& c) {
     return it;
   }
   if (res.chol_fail) c.status |= ST_CHOL_FAIL;
-  if (!res.converged) {
+  if (!res.converged) {   // finished by the cluster's double-float rescue
     c.status |= ST_FP64_RESCUE;
-    const int d = stage_pcg_df<M, kClThreads>(c, res.eta0, c.P->opt.pcg_max_iters);
-    c.df_iters += d;
-    it += d;
+    if (res.df_breakdown) c.status |= ST_PCG_BREAKDOWN;
+    if (!res.df_converged) c.status |= ST_PCG_MAXITER;
+    c.df_iters += res.df_it;
+    it += res.df_it;
   }
   return it;
 }

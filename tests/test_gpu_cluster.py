@@ -146,3 +146,19 @@ def test_cluster_and_single_team_forms_agree():
     if same.any():
         assert rel_err(g1["z"][same], g2["z"][same]).max() <= Z_GATE
     b1.close(); b2.close()
+
+
+def test_double_float_rescue_on_the_cluster():
+    """OCPs whose FP32 iteration stagnates are finished by the double-float PCG on the cluster
+    (status bit 64); those solutions match the FP64 oracle's replay like the others."""
+    w = workloads.rigid_body_config(B=64, T=128, seed=3, sqp_iters=5)
+    b, g = gpu_solve(w, pcg_tol=1e-7)
+    assert b.get_cluster()["ctas_per_cluster"] > 0
+    assert not (g["status"] & BAD).any(), g["status"]
+    rescued = np.where(g["status"] & 64)[0]
+    assert rescued.size > 0, "no OCP of this batch needed the rescue"
+    pick = np.concatenate([rescued[:4], np.setdiff1d(np.arange(w.B), rescued)[:2]])
+    sub = w.subset(pick)
+    res = replay_check(sub, g["z"][pick], g["alpha"][pick])
+    assert_replay_parity(f"cluster rescue ({rescued.size} rescued)", res, Z_GATE)
+    b.close()
