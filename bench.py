@@ -90,7 +90,7 @@ def throughput(world, steps, seconds):
 # bench step (the command and counters are summarised under profiles/), with the hash of the
 # kernel sources it was taken on; reported only while the sources still hash the same.  The hash
 # ignores comments and whitespace, so only an edit of the code itself invalidates a capture.
-TRAFFIC_CAPTURE = {"src_sha256_16": "695a935c6e8c0663", "bytes_per_launch": 630784 + 131072}
+TRAFFIC_CAPTURE = {"src_sha256_16": "f743c243c84d5bf3", "bytes_per_launch": 631552 + 128256}
 
 
 def _code_tokens(text):
@@ -678,6 +678,24 @@ def suite(path):
                                                                         ms=tuned["ms"]),
                               table=tuned.get("table"))
     b.close()
+
+    # 12-state rigid body, 64 OCPs, T = 128, 5 SQP iterations: the thread-block cluster form
+    # (automatic shape) against the one-team form from global memory and the plain form
+    w = workloads.rigid_body_config(B=64, T=128, seed=3, sqp_iters=5)
+    rb = {}
+    for name, cl in (("cluster", 0), ("one_team", 1)):
+        b = OCPBatch(("rigid_body12", 12, 4, 128, w.dt), batch=64, device=dev, sqp_iters=5, line_search=1,
+                     pcg_tol=PCG_TOL, warm_start=0, cluster_ctas=cl)
+        inp = (t(w.x_s), t(w.theta), t(w.x_ref))
+        z = b.solve(*inp)["z"]
+        dl = torch.zeros_like(z)
+        dl.view(64, -1)[:, 12] = 1.0
+        rb[name] = _fused_vs_plain(b, inp, dl, 3, 64) if name == "cluster" else {}
+        tf, _ = _timed(lambda: b.solve(*inp, want_stats=False), 3)
+        tb, _ = _timed(lambda: b.vjp(dl, want_stats=False), 3)
+        rb[name].update(fwd_ms=tf * 1e3, vjp_ms=tb * 1e3, cluster=b.get_cluster())
+        b.close()
+    out["rigid_body_b64_t128"] = rb
 
     # vehicle: 1024 single-track OCPs, T = 100, dt = 0.02, forward + backward
     w = workloads.vehicle_config(B=1024, T=100, seed=0, sqp_iters=SQP_ITERS)
