@@ -162,3 +162,39 @@ def test_double_float_rescue_on_the_cluster():
     res = replay_check(sub, g["z"][pick], g["alpha"][pick])
     assert_replay_parity(f"cluster rescue ({rescued.size} rescued)", res, Z_GATE)
     b.close()
+
+
+def test_cluster_stored_blocks_backward_matches_recompute():
+    """Stored-Schur mode on a cluster handle: the forward keeps the blocks at the returned z and
+    the vjp's cluster PCG reads them instead of forming them; the gradient equals the recompute
+    mode's."""
+    w = workloads.rigid_body_config(B=3, T=90, seed=17, sqp_iters=2)
+    b1, g1 = gpu_solve(w, store_schur=0)
+    b2, g2 = gpu_solve(w, store_schur=1)
+    assert b2.get_cluster()["ctas_per_cluster"] > 0
+    assert np.array_equal(g1["z"], g2["z"])
+    dl = w.dl_dz(g1["z"])
+    v1, v2 = gpu_vjp(b1, w, dl), gpu_vjp(b2, w, dl)
+    assert not ((v1["status"] | v2["status"]) & BAD).any()
+    assert rel_err(v2["dtheta"], v1["dtheta"]).max() <= 1e-5
+    ref = oracle_vjp(to_ocp(w), g2["z"], g2["lam"], dl)
+    assert rel_err(v2["dtheta"], ref["dtheta"]).max() <= G_GATE
+    b1.close(); b2.close()
+
+
+def test_cluster_exact_hessian_backward():
+    """Exact-Hessian backward (Riccati on CTA 0; OCPs whose reduced Hessian is not positive
+    definite take the Gauss-Newton path, whose PCG runs on the cluster) after a cluster forward."""
+    w = workloads.rigid_body_config(B=3, T=70, seed=19, sqp_iters=3)
+    b, g = gpu_solve(w, exact_hessian=1)
+    assert b.get_cluster()["ctas_per_cluster"] > 0
+    dl = w.dl_dz(g["z"])
+    gv = gpu_vjp(b, w, dl)
+    ocp = to_ocp(w)
+    exact = oracle_vjp(ocp, g["z"], g["lam"], dl, hessian="exact")
+    gn = oracle_vjp(ocp, g["z"], g["lam"], dl, hessian="gn")
+    flagged = (gv["status"] & 128) != 0
+    ref = np.where(flagged[:, None], gn["dtheta"], exact["dtheta"])
+    assert not (gv["status"] & BAD).any()
+    assert rel_err(gv["dtheta"], ref).max() <= G_GATE
+    b.close()
