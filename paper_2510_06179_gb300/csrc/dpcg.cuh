@@ -1,10 +1,11 @@
-// a4 distributed over a thread-block cluster: Algorithm 4 for one OCP whose workspace does not
-// fit in one CTA's shared memory (12-state rigid body, T up to a few hundred).  CTA 0 of the
-// cluster (the leader) runs every other stage of the SQP iteration and the backward pass from the
-// OCP's global-memory workspace, as the single-team kernel does.  At each PCG solve it hands the
-// solve to all CTAs of the cluster: CTA r copies the knots [r KC, (r+1) KC) of the S and Phi^-1
-// blocks, the factors A_t, B_t and the FP64 vectors into its own shared memory, and the PCG then
-// runs with every block resident on chip:
+// a2 (blocks), a3 and a4 distributed over a thread-block cluster: Algorithm 4 for one OCP whose
+// workspace does not fit in one CTA's shared memory (12-state rigid body, T up to a few hundred).
+// CTA 0 of the cluster (the leader) runs every other stage of the SQP iteration and the backward
+// pass from the OCP's global-memory workspace, as the single-team kernel does.  At each PCG solve
+// it hands the solve to all CTAs of the cluster: CTA r copies the factors A_t, B_t and the FP64
+// vectors of the knots [r KC, (r+1) KC) into its own shared memory, forms their Schur and
+// preconditioner blocks there (or reads stored ones), and the PCG then runs with every block
+// resident on chip:
 //   - knot k's row of S p (and of Phi^-1 r) needs p_{k-1} and the product with block k+1; a CTA
 //     keeps the first block of the next CTA as a halo copy, and the owner of a boundary knot
 //     sends the vector values its neighbours need into their shared memory along with the next
@@ -18,9 +19,8 @@
 //     thread forms the values of the three knots its block row reads, from double-buffered
 //     vectors), so an iteration synchronises only at its two all-reduces;
 //   - reliable updates evaluate the FP64 true residual gamma - H G^-1 H^T lambda from the
-//     factors (hp_apply's two passes, distributed the same way) and the stagnation test hands
-//     the solve back to the leader, which finishes it with the double-float rescue from global
-//     memory, exactly as the single-team kernel does.
+//     factors (hp_apply's two passes, distributed the same way); when the stagnation test fires,
+//     the double-float PCG (stage_pcg_df's iteration) continues on the cluster the same way.
 // Every wait on another CTA is an mbarrier wait with a time limit; when one runs out the CTA
 // stops waiting from then on, and the OCP is flagged (ST_SYNC_TIMEOUT).
 #pragma once
