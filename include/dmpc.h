@@ -136,7 +136,8 @@ typedef struct {
                           and (S u)^T u per iteration, S p by recurrence; equal in exact arithmetic);
                           single-warp teams (nx <= 4, K <= 64), the others behave as 0; default 0 */
   int cluster_ctas;    /* OCPs whose workspace does not fit in one thread block's shared memory (12-state
-                          rigid body): 0 = run each on a thread-block cluster when one fits (its Schur
+                          rigid body) and OCPs with nx >= 16 (LQ nx 16): 0 = run each on a thread-block
+                          cluster when one fits (its Schur
                           blocks, preconditioner and PCG solves distributed over the shared memory of the
                           cluster's CTAs, about 40 knots per CTA), 1 = never (one team from global memory),
                           2..8 = clusters of that many CTAs (at most 42 knots per CTA, else one team);

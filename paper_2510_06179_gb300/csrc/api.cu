@@ -280,6 +280,7 @@ static dmpc_err configure_cluster(dmpc_handle* h, int maxK) {
   h->fn = fn;
   h->plain_fn = pfn;
   h->max_ws_floats = ws;
+  h->use_gws = true;   // the leader's workspace is a global slot per cluster
   h->use_cluster = true;
   h->cl_ncta = ncta;
   h->cl_kc = kc;
@@ -372,7 +373,10 @@ static dmpc_err configure_tiling(dmpc_handle* h, int team, int tpb) {
   h->fn = fn;
   h->plain_fn = pfn;
   h->use_cluster = false;
-  if (h->use_gws && h->uniform && team_is_default && h->opt.cluster_ctas != 1 && !has_implicit_desc(h)) {
+  // the cluster form where one CTA cannot hold the workspace, and for nx >= 16, whose one-warp team
+  // would carry four 16 x 16 blocks per lane even when the workspace fits
+  if ((h->use_gws || maxnx >= 16) && h->uniform && team_is_default && h->opt.cluster_ctas != 1 &&
+      !has_implicit_desc(h)) {
     dmpc_err ce = configure_cluster(h, maxK);
     if (ce != DMPC_OK) return ce;
   }

@@ -1,6 +1,7 @@
 // Fused and plain kernels for LQ OCPs with nx = 16, nu = 8 (the RL benchmark's problems 5 and 6,
-// App. B.1), on 32-thread teams only: one instantiation of this size takes minutes of nvcc, so
-// the other team sizes register nothing and the tiling falls back to 32 threads.
+// App. B.1) on 32-thread teams; the 256-thread ones are compiled with the cluster kernel
+// (cl_lq16.cu), and the other team sizes register nothing (an instantiation of this size takes
+// about two minutes of nvcc).
 #include "launch_impl.cuh"
 
 #ifndef DMPC_TEAM

@@ -51,6 +51,8 @@ struct ClusterEntry {
   ClusterOccFn max_clusters;
 };
 int register_cluster_rigid_body(ClusterEntry*);
+int register_cluster_lq16(ClusterEntry*);
+int register_lq16_team256(KernelEntry*);   // the 256-thread LQ nx 16 kernels live in the cluster unit
 constexpr int kMaxClusterEntries = 8;
 int collect_cluster_entries(ClusterEntry* out);
 

@@ -39,12 +39,14 @@ int collect_kernel_entries(KernelEntry* out) {
   DMPC_COLLECT(attitude)
   DMPC_COLLECT(mixed)
 #undef DMPC_COLLECT
+  n += register_lq16_team256(out + n);
   return n;
 }
 
 int collect_cluster_entries(ClusterEntry* out) {
   int n = 0;
   n += register_cluster_rigid_body(out + n);
+  n += register_cluster_lq16(out + n);
   return n;
 }
 }  // namespace dmpc

@@ -198,3 +198,23 @@ def test_cluster_exact_hessian_backward():
     assert not (gv["status"] & BAD).any()
     assert rel_err(gv["dtheta"], ref).max() <= G_GATE
     b.close()
+
+
+def test_lq_nx16_cluster_matches_the_oracle():
+    """LQ with nx 16, nu 8, T 30 (the RL table's problems 5 and 6) runs on a cluster (a one-warp team
+    would carry four 16 x 16 blocks per lane); one SQP step solves the QP exactly, compared with the
+    oracle's direct KKT solve, and the gradient with the oracle's VJP."""
+    from oracle.sqp import sqp as oracle_sqp
+    w = workloads.lq_config(B=6, T=30, nx=16, nu=8, seed=4, c_var=0.01)
+    b, g = gpu_solve(w, pcg_tol=1e-8)
+    assert b.get_cluster()["ctas_per_cluster"] > 0
+    assert not (g["status"] & BAD & ~4).any(), g["status"]
+    ref = oracle_sqp(to_ocp(w), 1, line_search_on=False)
+    ez = rel_err(g["z"], ref["z"])
+    dl = w.dl_dz(g["z"])
+    gv = gpu_vjp(b, w, dl)
+    gr = oracle_vjp(to_ocp(w), g["z"], g["lam"], dl)
+    eg = rel_err(gv["dtheta"], gr["dtheta"])
+    print(f"LQ nx 16 cluster: z err {ez.max():.2e}, dtheta err {eg.max():.2e}, {b.get_cluster()}")
+    assert ez.max() <= Z_GATE and eg.max() <= G_GATE
+    b.close()
