@@ -280,7 +280,8 @@ dmpc_err dmpc_set_solution(dmpc_handle* h, const float* z, const float* lam, con
 dmpc_err dmpc_set_stream(dmpc_handle* h, void* cuda_stream);
 
 /* Override the tiling: threads per OCP (32/64/128/256) and OCPs per block (>= 1).  An explicit
- * tiling runs every OCP on one team (no cluster form). */
+ * tiling runs every OCP on one team (no cluster form); (0, 0) restores the automatic choice made
+ * at creation, the cluster form included. */
 dmpc_err dmpc_set_tiling(dmpc_handle* h, int team_threads, int teams_per_block);
 
 /* Current tiling and per-team workspace: team threads, teams per block, grid size, dynamic

@@ -73,7 +73,8 @@ def _time_step(batch, inputs, dl_dz, reps):
 
 
 def tune(batch, inputs, dl_dz=None, reps=3, use_cache=True, teams=TEAMS, tpbs=TPBS):
-    """Choose (team_threads, teams_per_block) for `batch` by timing; applies and returns it.
+    """Choose (team_threads, teams_per_block) for `batch` by timing; applies and returns it
+    ((0, 0): the automatic choice, which includes the thread-block cluster form).
 
     inputs: (x_s, theta, x_ref) device tensors for batch.solve; dl_dz: optional loss gradient
     for a timed backward.  Returns dict(team_threads, teams_per_block, ms, table)."""
@@ -84,6 +85,11 @@ def tune(batch, inputs, dl_dz=None, reps=3, use_cache=True, teams=TEAMS, tpbs=TP
         batch.set_tiling(best["team_threads"], best["teams_per_block"])
         return dict(best, cached=True)
     table = []
+    # the automatic choice first (team_threads = teams_per_block = 0; the only candidate that can
+    # be the thread-block cluster form), then every explicit tiling
+    batch.set_tiling(0, 0)
+    table.append(dict(team_threads=0, teams_per_block=0, ms=_time_step(batch, inputs, dl_dz, reps),
+                      auto=batch.get_tiling(), cluster=batch.get_cluster()))
     for team in teams:
         for tpb in tpbs:
             if team * tpb > 256:

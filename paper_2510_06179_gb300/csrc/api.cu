@@ -1010,6 +1010,7 @@ extern "C" dmpc_err dmpc_set_stream(dmpc_handle* h, void* s) {
 
 extern "C" dmpc_err dmpc_set_tiling(dmpc_handle* h, int team_threads, int teams_per_block) {
   if (!h) return DMPC_E_ARG;
+  if (team_threads == 0 && teams_per_block == 0) return configure_tiling(h, 0, 0);   // the automatic choice
   if (team_threads != 32 && team_threads != 64 && team_threads != 128 && team_threads != 256)
     return fail(h, DMPC_E_ARG, "team_threads must be 32, 64, 128 or 256");
   if (teams_per_block < 1 || team_threads * teams_per_block > 256)

@@ -50,7 +50,7 @@ def test_autotuned_tiling_keeps_results():
     base = b.solve(*inp)["z"].clone()
     torch.cuda.synchronize()
     res = autotune.tune(b, inp, reps=1, use_cache=False, teams=(64, 128), tpbs=(1, 2))
-    assert res["team_threads"] in (64, 128) and len(res["table"]) >= 2
+    assert res["team_threads"] in (0, 64, 128) and len(res["table"]) >= 3   # 0: the automatic choice
     z = b.solve(*inp)["z"]
     torch.cuda.synchronize()
     zz, bb = z.cpu().numpy().astype(np.float64), base.cpu().numpy().astype(np.float64)

@@ -218,3 +218,26 @@ def test_lq_nx16_cluster_matches_the_oracle():
     print(f"LQ nx 16 cluster: z err {ez.max():.2e}, dtheta err {eg.max():.2e}, {b.get_cluster()}")
     assert ez.max() <= Z_GATE and eg.max() <= G_GATE
     b.close()
+
+
+def test_autotuner_keeps_the_cluster_form():
+    """The automatic tiling is the autotuner's first candidate, so a rigid-body batch with a long
+    horizon keeps the cluster form (every explicit tiling runs one team from global memory); an
+    explicit tiling and then (0, 0) restore the automatic choice."""
+    import torch
+    from paper_2510_06179_gb300 import autotune
+    w = workloads.rigid_body_config(B=4, T=100, seed=23, sqp_iters=1)
+    b = make_batch(w, pcg_tol=1e-7)
+    auto = b.get_cluster()
+    assert auto["ctas_per_cluster"] > 0
+    b.set_tiling(256, 1)
+    assert b.get_cluster()["ctas_per_cluster"] == 0
+    b.set_tiling(0, 0)
+    assert b.get_cluster() == auto
+    inp = (dev(w.x_s), dev(w.theta), dev(w.x_ref))
+    res = autotune.tune(b, inp, reps=1, use_cache=False, teams=(128, 256), tpbs=(1,))
+    assert res["table"][0]["team_threads"] == 0
+    print("autotune table (ms):", [(r["team_threads"], r["teams_per_block"], round(r["ms"], 2)) for r in res["table"]])
+    assert (res["team_threads"], res["teams_per_block"]) == (0, 0)
+    assert b.get_cluster() == auto
+    b.close()
