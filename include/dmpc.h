@@ -23,7 +23,8 @@
  *    Costs: c_t^x(x) = 1/2 (x - x_ref,t)^T diag(Q) (x - x_ref,t)  (diag(Q_T) at t = T),
  *           c_t^u(u) = 1/2 u^T diag(R) u.
  *  - Models (f_t = x_{t+1} - Phi_t(x_t, u_t), Phi one RK4 / Euler step, or affine):
- *      LQ           nx, nu in {(2,1),(3,2),(4,1),(8,4),(16,8)} ((16,8): 32-thread teams); p_s = 0; per knot
+ *      LQ           nx, nu in {(2,1),(3,2),(4,1),(8,4),(16,8)} ((16,8): 32-thread teams or the cluster
+ *                   form); p_s = 0; per knot
  *                   p_k = nx*nx + nx*nu + nx: Abar_t (row-major), Bbar_t, c_t
  *      PENDULUM     nx 2, nu 1, params (m, L)                 RK4
  *      CARTPOLE     nx 4, nu 1, params (m_pole, L), m_cart 1  RK4
