@@ -140,8 +140,10 @@ typedef struct {
                           rigid body) and OCPs with nx >= 16 (LQ nx 16): 0 = run each on a thread-block
                           cluster when one fits (its Schur
                           blocks, preconditioner and PCG solves distributed over the shared memory of the
-                          cluster's CTAs, about 40 knots per CTA), 1 = never (one team from global memory),
-                          2..8 = clusters of that many CTAs (at most 42 knots per CTA, else one team);
+                          cluster's CTAs, about 40 knots per CTA, fewer where shared memory holds fewer:
+                          25 for LQ nx 16, nu 8), 1 = never (one team from global memory),
+                          2..8 = clusters of that many CTAs (at most 42 knots per CTA for nx 12, 32 for
+                          nx 16, and what one CTA's shared memory holds, else one team);
                           applies with team_threads = 0; default 0 */
 } dmpc_options;
 

@@ -236,8 +236,8 @@ static bool has_implicit_desc(const dmpc_handle* h) {
 
 // Cluster form for OCPs whose workspace does not fit in one CTA's shared memory: one cluster of
 // ncta CTAs per OCP, each holding ceil(K / ncta) knots of the PCG's blocks in shared memory.
-// cluster_ctas = 0 chooses ncta from the longest horizon: about 40 knots per CTA (at most 8 CTAs),
-// the fewest CTAs that hold the OCP, since an iteration's cost per CTA grows slowly with its knots
+// cluster_ctas = 0 chooses ncta from the longest horizon: about 40 knots per CTA, or as many as one
+// CTA's shared memory holds where that is fewer (at most 8 CTAs): the fewest CTAs that hold the OCP, since an iteration's cost per CTA grows slowly with its knots
 // (its chain is the two all-reduces) and fewer CTAs per OCP leave more SMs to the rest of a batch.
 // Leaves the single-team form in place when no cluster kernel fits.
 static dmpc_err configure_cluster(dmpc_handle* h, int maxK) {
@@ -246,12 +246,22 @@ static dmpc_err configure_cluster(dmpc_handle* h, int maxK) {
     if (e.model == h->model0 && e.nx == h->nx0 && e.nu == h->nu0) ce = &e;
   if (!ce) return DMPC_OK;
   const int kc_max = cl_max_kc(h->nx0);
+  auto cl_bytes = [&](int kc) { return (size_t)cl_layout(h->nx0, h->nu0, kc).total * sizeof(float); };
   int ncta = h->opt.cluster_ctas;
-  if (ncta == 0) ncta = std::min(kClMaxCtas, std::max(2, (maxK + 39) / 40));
+  if (ncta == 0) {
+    // from ~40 knots per CTA up, the first count whose share fits the thread and shared-memory
+    // limits (LQ with nx 16 holds at most 25 knots per CTA)
+    ncta = std::min(kClMaxCtas, std::max(2, (maxK + 39) / 40));
+    while (ncta < kClMaxCtas) {
+      const int k = (maxK + ncta - 1) / ncta;
+      if (k <= kc_max && cl_bytes(k) <= (size_t)h->smem_optin) break;
+      ++ncta;
+    }
+  }
   if (ncta < 2) return DMPC_OK;
   const int kc = (maxK + ncta - 1) / ncta;
   if (kc > kc_max) return DMPC_OK;
-  const size_t smem = (size_t)cl_layout(h->nx0, h->nu0, kc).total * sizeof(float);
+  const size_t smem = cl_bytes(kc);
   if (smem > (size_t)h->smem_optin) return DMPC_OK;
   const int fit = ce->max_clusters(ncta, smem);
   if (fit < 1) return DMPC_OK;

@@ -207,7 +207,7 @@ def test_lq_nx16_cluster_matches_the_oracle():
     from oracle.sqp import sqp as oracle_sqp
     w = workloads.lq_config(B=6, T=30, nx=16, nu=8, seed=4, c_var=0.01)
     b, g = gpu_solve(w, pcg_tol=1e-8)
-    assert b.get_cluster()["ctas_per_cluster"] > 0
+    assert b.get_cluster()["ctas_per_cluster"] == 2
     assert not (g["status"] & BAD & ~4).any(), g["status"]
     ref = oracle_sqp(to_ocp(w), 1, line_search_on=False)
     ez = rel_err(g["z"], ref["z"])
