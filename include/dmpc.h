@@ -299,6 +299,18 @@ dmpc_err dmpc_get_tiling(const dmpc_handle* h, int* team_threads, int* teams_per
  * the OCP from its global workspace, and every CTA takes part in its PCG solves. */
 dmpc_err dmpc_get_cluster(const dmpc_handle* h, int* ctas_per_cluster, int* knots_per_cta, int* clusters);
 
+/* The cluster shape the library takes for OCPs of nx states, nu inputs and at most `knots` knots
+ * (T + 1) under dmpc_options.cluster_ctas = cluster_ctas, on a device whose CTAs may use
+ * smem_per_cta bytes of shared memory (the opt-in limit: 232448 on GB300): CTAs per cluster, knots
+ * of the S and Phi^-1 blocks (Eq. 8-10) each CTA holds, and the dynamic shared memory of one CTA.
+ * All 0 when no shape fits the thread and shared-memory limits.  Host arithmetic only: touches no
+ * GPU and needs none.  Whether a handle takes the shape also depends on its model having a cluster
+ * kernel (12-state rigid body, LQ with nx 16) and on its one-team workspace; dmpc_get_cluster
+ * reports what a handle took.  Each output pointer may be NULL.  DMPC_E_ARG: nx, nu or knots < 1,
+ * cluster_ctas outside 0..8, smem_per_cta < 0. */
+dmpc_err dmpc_cluster_shape(int nx, int nu, int knots, int cluster_ctas, long long smem_per_cta,
+                            int* ctas_per_cluster, int* knots_per_cta, long long* smem_bytes);
+
 /* Release the handle and its device memory (synchronises its stream). NULL is ignored. */
 void dmpc_destroy(dmpc_handle* h);
 

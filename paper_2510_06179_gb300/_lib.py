@@ -42,6 +42,7 @@ SIGNATURES = {
     "dmpc_device_bytes": (ctypes.c_longlong, [P]),
     "dmpc_inspect_offsets": (c_int, [P, P]),
     "dmpc_get_cluster": (c_int, [P, P, P, P]),
+    "dmpc_cluster_shape": (c_int, [c_int, c_int, c_int, c_int, c_ll, P, P, P]),
     "dmpc_solve_noalloc": (c_int, [ctypes.POINTER(dmpc_ocp_desc), c_int, ctypes.POINTER(dmpc_options), P,
                                    P, P, P, P, P, P, P, P, P, P]),
     "dmpc_set_solution": (c_int, [P, P, P, P, P, P]),

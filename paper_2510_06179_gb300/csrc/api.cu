@@ -234,35 +234,54 @@ static bool has_implicit_desc(const dmpc_handle* h) {
   return false;
 }
 
-// Cluster form for OCPs whose workspace does not fit in one CTA's shared memory: one cluster of
-// ncta CTAs per OCP, each holding ceil(K / ncta) knots of the PCG's blocks in shared memory.
-// cluster_ctas = 0 chooses ncta from the longest horizon: about 40 knots per CTA, or as many as one
-// CTA's shared memory holds where that is fewer (at most 8 CTAs): the fewest CTAs that hold the OCP, since an iteration's cost per CTA grows slowly with its knots
-// (its chain is the two all-reduces) and fewer CTAs per OCP leave more SMs to the rest of a batch.
-// Leaves the single-team form in place when no cluster kernel fits.
-static dmpc_err configure_cluster(dmpc_handle* h, int maxK) {
-  const ClusterEntry* ce = nullptr;
-  for (auto& e : cluster_registry())
-    if (e.model == h->model0 && e.nx == h->nx0 && e.nu == h->nu0) ce = &e;
-  if (!ce) return DMPC_OK;
-  const int kc_max = cl_max_kc(h->nx0);
-  auto cl_bytes = [&](int kc) { return (size_t)cl_layout(h->nx0, h->nu0, kc).total * sizeof(float); };
-  int ncta = h->opt.cluster_ctas;
+// Shape of the cluster form (Algorithm 4 distributed over a thread-block cluster) for OCPs of nx
+// states, nu inputs and at most maxK knots: ncta CTAs per OCP, each holding kc = ceil(maxK / ncta)
+// knots of the PCG's blocks in smem bytes of shared memory.  req = 0 chooses ncta from the longest
+// horizon: about 40 knots per CTA, or as many as one CTA's shared memory holds where that is fewer
+// (at most 8 CTAs): the fewest CTAs that hold the OCP, since an iteration's cost per CTA grows
+// slowly with its knots (its chain is the two all-reduces) and fewer CTAs per OCP leave more SMs to
+// the rest of a batch.  ncta = 0 when no shape fits the thread and shared-memory limits.
+static void cluster_shape(int nx, int nu, int maxK, int req, size_t smem_limit, int* ncta_out, int* kc_out,
+                          size_t* smem_out) {
+  *ncta_out = 0;
+  *kc_out = 0;
+  *smem_out = 0;
+  if (nx < kClRows || nx % kClRows != 0 || nu < 1 || maxK < 1) return;
+  const int kc_max = cl_max_kc(nx);
+  auto cl_bytes = [&](int kc) { return (size_t)cl_layout(nx, nu, kc).total * sizeof(float); };
+  int ncta = req;
   if (ncta == 0) {
     // from ~40 knots per CTA up, the first count whose share fits the thread and shared-memory
     // limits (LQ with nx 16 holds at most 25 knots per CTA)
     ncta = std::min(kClMaxCtas, std::max(2, (maxK + 39) / 40));
     while (ncta < kClMaxCtas) {
       const int k = (maxK + ncta - 1) / ncta;
-      if (k <= kc_max && cl_bytes(k) <= (size_t)h->smem_optin) break;
+      if (k <= kc_max && cl_bytes(k) <= smem_limit) break;
       ++ncta;
     }
   }
-  if (ncta < 2) return DMPC_OK;
+  if (ncta < 2 || ncta > kClMaxCtas) return;
   const int kc = (maxK + ncta - 1) / ncta;
-  if (kc > kc_max) return DMPC_OK;
+  if (kc > kc_max) return;
   const size_t smem = cl_bytes(kc);
-  if (smem > (size_t)h->smem_optin) return DMPC_OK;
+  if (smem > smem_limit) return;
+  *ncta_out = ncta;
+  *kc_out = kc;
+  *smem_out = smem;
+}
+
+// Cluster form for OCPs whose workspace does not fit in one CTA's shared memory: one cluster of
+// ncta CTAs per OCP in the shape cluster_shape gives.  Leaves the single-team form in place when
+// no cluster kernel fits.
+static dmpc_err configure_cluster(dmpc_handle* h, int maxK) {
+  const ClusterEntry* ce = nullptr;
+  for (auto& e : cluster_registry())
+    if (e.model == h->model0 && e.nx == h->nx0 && e.nu == h->nu0) ce = &e;
+  if (!ce) return DMPC_OK;
+  int ncta = 0, kc = 0;
+  size_t smem = 0;
+  cluster_shape(h->nx0, h->nu0, maxK, h->opt.cluster_ctas, (size_t)h->smem_optin, &ncta, &kc, &smem);
+  if (ncta == 0) return DMPC_OK;
   const int fit = ce->max_clusters(ncta, smem);
   if (fit < 1) return DMPC_OK;
   // the leader runs the OCP as a 256-thread team: that team's kernels and workspace layout
@@ -1035,6 +1054,19 @@ extern "C" dmpc_err dmpc_get_tiling(const dmpc_handle* h, int* team_threads, int
   if (teams_per_block) *teams_per_block = h->tpb;
   if (grid) *grid = h->grid;
   if (smem_bytes) *smem_bytes = (long long)h->smem;
+  return DMPC_OK;
+}
+
+extern "C" dmpc_err dmpc_cluster_shape(int nx, int nu, int knots, int cluster_ctas, long long smem_per_cta,
+                                       int* ctas_per_cluster, int* knots_per_cta, long long* smem_bytes) {
+  if (nx < 1 || nu < 1 || knots < 1 || cluster_ctas < 0 || cluster_ctas > kClMaxCtas || smem_per_cta < 0)
+    return DMPC_E_ARG;
+  int ncta = 0, kc = 0;
+  size_t smem = 0;
+  cluster_shape(nx, nu, knots, cluster_ctas, (size_t)smem_per_cta, &ncta, &kc, &smem);
+  if (ctas_per_cluster) *ctas_per_cluster = ncta;
+  if (knots_per_cta) *knots_per_cta = kc;
+  if (smem_bytes) *smem_bytes = (long long)smem;
   return DMPC_OK;
 }
 

@@ -49,6 +49,16 @@ def default_options(**kw):
     return o
 
 
+def cluster_shape(nx, nu, T, cluster_ctas=0, smem_per_cta=232448):
+    """Shape of the cluster form for OCPs of nx states, nu inputs and horizon T (dmpc_cluster_shape;
+    host arithmetic, no GPU): CTAs per cluster, knots per CTA and one CTA's dynamic shared memory,
+    all 0 when no shape fits.  smem_per_cta: the device's opt-in shared memory per block."""
+    v = [ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()]
+    _lib.check(_lib.load().dmpc_cluster_shape(nx, nu, T + 1, cluster_ctas, smem_per_cta,
+                                              *[ctypes.byref(x) for x in v]))
+    return dict(ctas_per_cluster=v[0].value, knots_per_cta=v[1].value, smem_bytes=v[2].value)
+
+
 class OCPBatch:
     """A batch of OCPs handled by one C-ABI handle (dmpc_create_problem_batch).
 
