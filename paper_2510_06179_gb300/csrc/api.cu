@@ -246,7 +246,8 @@ static void cluster_shape(int nx, int nu, int maxK, int req, size_t smem_limit, 
   *ncta_out = 0;
   *kc_out = 0;
   *smem_out = 0;
-  if (nx < kClRows || nx % kClRows != 0 || nu < 1 || maxK < 1) return;
+  // (bounds far above any cluster shape keep the layout's int arithmetic from overflowing)
+  if (nx < kClRows || nx % kClRows != 0 || nx > 512 || nu < 1 || nu > 512 || maxK < 1 || maxK > (1 << 20)) return;
   const int kc_max = cl_max_kc(nx);
   auto cl_bytes = [&](int kc) { return (size_t)cl_layout(nx, nu, kc).total * sizeof(float); };
   int ncta = req;

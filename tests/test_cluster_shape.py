@@ -82,3 +82,5 @@ def test_bad_arguments():
         assert lib.dmpc_cluster_shape(*args, None, None, None) == 1, args
     assert lib.dmpc_cluster_shape(12, 4, 257, 0, SMEM, None, None, None) == 0
     assert _shape(13, 4, 257) == (0, 0, 0)   # rows are taken in pairs: odd nx has no cluster form
+    for big in ((12, 4, 2**31 - 1), (2**20, 4, 257), (12, 2**20, 257)):   # no overflow, no shape
+        assert _shape(*big) == (0, 0, 0)
